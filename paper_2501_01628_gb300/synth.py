@@ -1,0 +1,202 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module only *generates inputs*: scalar volumes, transfer-function tables,
+camera descriptions and the random cut fractions of a kd partition. It holds
+none of the rendering method's arithmetic (no ray generation, sampling,
+classification, accumulation or compositing), so both sides consume identical
+bytes without sharing any of the computation under test.
+
+The paper (Sec. 4) renders the NASA Mars Lander mixed-element data set, which
+is not available; these volumes stand in for it with the shapes, sizes and
+partition structure of the workloads (Sec. 2.2: data spatially distributed
+across ranks, possibly unevenly; Sec. 4: 36 GPUs, several parts per GPU).
+
+Draw order is part of the contract: every generator takes a
+``numpy.random.Generator`` (PCG64 via ``default_rng(seed)``) and documents
+which draws it makes, in which order.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Volumes (x fastest: array index [z, y, x])
+# --------------------------------------------------------------------------
+
+
+@dataclass(frozen=True)
+class Blobs:
+    centers: np.ndarray  # (n, 3) xyz in [0,1]^3 (world units of the unit cube)
+    sigmas: np.ndarray   # (n,)
+    amps: np.ndarray     # (n,)
+
+
+def draw_blobs(rng: np.random.Generator, n: int) -> Blobs:
+    """Draws, in order: n*3 centers U[0,1] (row-major, xyz per blob),
+    n sigmas U[0.05, 0.15], n amplitudes U[0.2, 1.0]."""
+    centers = rng.uniform(0.0, 1.0, size=(n, 3))
+    sigmas = rng.uniform(0.05, 0.15, size=n)
+    amps = rng.uniform(0.2, 1.0, size=n)
+    return Blobs(centers, sigmas, amps)
+
+
+def _voxel_centers(n: int) -> np.ndarray:
+    return (np.arange(n, dtype=np.float64) + 0.5) / n
+
+
+def blob_volume(n: int, blobs: Blobs, offset: np.ndarray | None = None,
+                out: np.ndarray | None = None) -> np.ndarray:
+    """Sum of isotropic Gaussians a*exp(-|x-mu|^2/(2 sigma^2)) evaluated at the
+    voxel centres of an n^3 grid over [0,1]^3 (separable per axis, float64
+    factors, accumulated into float32 in z slabs to bound host memory)."""
+    x = _voxel_centers(n)
+    if out is None:
+        out = np.zeros((n, n, n), dtype=np.float32)
+    centers = blobs.centers if offset is None else blobs.centers + offset
+    for (cx, cy, cz), s, a in zip(centers, blobs.sigmas, blobs.amps):
+        gx = np.exp(-((x - cx) ** 2) / (2 * s * s))
+        gy = np.exp(-((x - cy) ** 2) / (2 * s * s))
+        gz = a * np.exp(-((x - cz) ** 2) / (2 * s * s))
+        plane = (gy[:, None] * gx[None, :]).astype(np.float32)
+        gz32 = gz.astype(np.float32)
+        step = max(1, (1 << 24) // (n * n))
+        for z0 in range(0, n, step):
+            z1 = min(n, z0 + step)
+            out[z0:z1] += gz32[z0:z1, None, None] * plane[None, :, :]
+    return out
+
+
+def _lerp_axis(a: np.ndarray, n: int, cells: int, axis: int) -> np.ndarray:
+    """Linear interpolation of lattice values along one axis onto the voxel
+    centres of an n-voxel axis (lattice spacing 1/cells over [0,1])."""
+    pos = _voxel_centers(n) * cells
+    i0 = np.minimum(np.floor(pos).astype(np.int64), cells - 1)
+    w = (pos - i0).astype(np.float32)
+    a0 = np.take(a, i0, axis=axis)
+    a1 = np.take(a, i0 + 1, axis=axis)
+    shape = [1] * a.ndim
+    shape[axis] = n
+    w = w.reshape(shape)
+    return a0 + w * (a1 - a0)
+
+
+def value_noise(n: int, rng: np.random.Generator, octaves: int = 6) -> np.ndarray:
+    """Fractal value noise normalised to [0,1].
+
+    Octave o (o = 0..octaves-1) has 4*2^o lattice cells per unit; its
+    (cells+1)^3 lattice values are drawn U[0,1] in octave order (array order
+    [z,y,x]) and trilinearly upsampled to the voxel centres; octaves are summed
+    with amplitude 0.5^o and the sum is min-max normalised."""
+    acc = np.zeros((n, n, n), dtype=np.float32)
+    for o in range(octaves):
+        cells = 4 * (2 ** o)
+        lat = rng.uniform(0.0, 1.0, size=(cells + 1,) * 3).astype(np.float32)
+        a = _lerp_axis(lat, n, cells, 2)
+        a = _lerp_axis(a, n, cells, 1)
+        a = _lerp_axis(a, n, cells, 0)
+        acc += np.float32(0.5 ** o) * a
+        del a
+    lo, hi = float(acc.min()), float(acc.max())
+    acc -= np.float32(lo)
+    acc *= np.float32(1.0 / (hi - lo))
+    return acc
+
+
+# --------------------------------------------------------------------------
+# Transfer function tables
+# --------------------------------------------------------------------------
+
+
+def random_tf(rng: np.random.Generator, n_entries: int = 256, n_points: int = 4,
+              alpha_max: float = 0.05) -> np.ndarray:
+    """Piecewise-linear RGBA table of n_entries (entry i sits at u = i/(n-1)).
+
+    Draws, in order: n_points positions U[0,1] (then sorted), n_points*3 rgb
+    U[0,1] (row-major), n_points alphas U[0, alpha_max]. Control points are
+    joined linearly; outside [x_0, x_last] the end values are held."""
+    xs = np.sort(rng.uniform(0.0, 1.0, size=n_points))
+    rgb = rng.uniform(0.0, 1.0, size=(n_points, 3))
+    alpha = rng.uniform(0.0, alpha_max, size=n_points)
+    ctrl = np.concatenate([rgb, alpha[:, None]], axis=1)
+    u = np.arange(n_entries, dtype=np.float64) / (n_entries - 1)
+    table = np.stack([np.interp(u, xs, ctrl[:, c]) for c in range(4)], axis=1)
+    return table.astype(np.float32)
+
+
+def constant_tf(rgba, n_entries: int = 256) -> np.ndarray:
+    return np.tile(np.asarray(rgba, dtype=np.float32)[None, :], (n_entries, 1))
+
+
+# --------------------------------------------------------------------------
+# Cameras (plain dicts; each side marshals them into its own struct)
+# --------------------------------------------------------------------------
+
+
+def ortho_camera_z(width: int, height: int, extent=(1.0, 1.0)) -> dict:
+    """Orthographic camera looking along +z whose image plane covers the
+    volume's xy extent exactly, placed on the z = 0 face."""
+    return dict(ortho=1, eye=(extent[0] / 2, extent[1] / 2, 0.0), dir=(0.0, 0.0, 1.0),
+                up=(0.0, 1.0, 0.0), fovy_deg=0.0, ortho_w=float(extent[0]),
+                ortho_h=float(extent[1]), width=int(width), height=int(height))
+
+
+def orbit_camera(width: int, height: int, azimuth_deg: float, radius: float = 1.8,
+                 elevation_deg: float = 20.0, fovy_deg: float = 60.0,
+                 center=(0.5, 0.5, 0.5)) -> dict:
+    """Perspective camera on a circle around the volume centre, looking at it,
+    +y up. azimuth 0 sits on the -z side looking towards +z."""
+    el = math.radians(elevation_deg)
+    az = math.radians(azimuth_deg)
+    c = np.asarray(center, dtype=np.float64)
+    eye = c + radius * np.array([math.cos(el) * math.sin(az), math.sin(el),
+                                 -math.cos(el) * math.cos(az)])
+    d = c - eye
+    return dict(ortho=0, eye=tuple(eye), dir=tuple(d), up=(0.0, 1.0, 0.0),
+                fovy_deg=float(fovy_deg), ortho_w=0.0, ortho_h=0.0,
+                width=int(width), height=int(height))
+
+
+ORBIT_AZIMUTHS = tuple(45.0 * i for i in range(8))
+
+
+# --------------------------------------------------------------------------
+# Partition randomness
+# --------------------------------------------------------------------------
+
+
+def kd_cut_fractions(rng: np.random.Generator, n_bricks: int, lo: float = 0.3,
+                     hi: float = 0.7) -> np.ndarray:
+    """n_bricks-1 cut fractions U[lo, hi], one per kd split in split order."""
+    return rng.uniform(lo, hi, size=max(0, n_bricks - 1))
+
+
+# --------------------------------------------------------------------------
+# Workload recipes (sizes and seeds of the five benchmark workloads)
+# --------------------------------------------------------------------------
+
+
+def small_blob_scene(n: int = 64, seed: int = 0, n_blobs: int = 8):
+    """64^3 blobs, 256-entry random TF (seed order: blobs then TF)."""
+    rng = np.random.default_rng(seed)
+    blobs = draw_blobs(rng, n_blobs)
+    vol = blob_volume(n, blobs)
+    tf = random_tf(rng)
+    return vol, tf
+
+
+def noise_blob_scene(n: int = 512, seed: int = 1, n_blobs: int = 16):
+    """Value noise (6 octaves) + 16 blobs, then a random TF (seed order:
+    noise lattices, blobs, TF)."""
+    rng = np.random.default_rng(seed)
+    vol = value_noise(n, rng)
+    blobs = draw_blobs(rng, n_blobs)
+    blob_volume(n, blobs, out=vol)
+    tf = random_tf(rng)
+    return vol, tf
+
+
+def volume_range(vol: np.ndarray):
+    return float(vol.min()), float(vol.max())
