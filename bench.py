@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the data-parallel volume rendering hot path on one GB300.
+
+One step = one composited frame: the per-brick emission-absorption march of
+all bricks plus the sort-last "over" composite, at the next of 8 orbit views.
+
+Workload (default): 512^3 float32 volume (6-octave value noise + 16 Gaussian
+blobs, seed 1) split into 36 bricks (4x3x3 grid), 1920x1080 perspective image
+(60 degree field of view) orbiting the volume, step 0.5 voxel, early ray
+termination at alpha 0.99, radix-k composite 4x3x3. Synthetic stand-in for the
+paper's distributed data set (36 GPUs in the paper's run, one brick each).
+
+value = executed ray samples per second over the timed frames (samples counted
+per view in an untimed pass). Inputs (560 MB of bricks) exceed the 129 MB L2.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank renders its own views of a replica of the volume
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray samples/s and composited frames/s at 1 GB300; % HBM roofline; vs FP64 oracle"
+UNIT = "samples/s"
+# FP32 operations the method performs per executed sample (position 8,
+# trilinear reconstruction 30, classification 19, accumulation 8, termination
+# test 1); the derivation is in the design doc.
+FLOPS_PER_SAMPLE = 66
+SMS, FP32_LANES = 152, 128
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name: str):
+    import numpy as np
+    from paper_2501_01628_gb300 import synth
+    if name == "small":
+        vol, tf = synth.small_blob_scene()
+        cams = [synth.ortho_camera_z(256, 256)]
+        return dict(name="small: 64^3 f32 blobs (8, seed 0), 2x2x2 bricks, 256x256 orthographic +z, "
+                         "step 0.5 voxel, no early termination, direct composite",
+                    vol=vol, tf=tf, part=dict(kind="grid", grid=(2, 2, 2)), cams=cams, step=0.5,
+                    ert=1.0, schedule=(), grid=(2, 2, 2))
+    vol, tf = synth.noise_blob_scene()
+    cams = [synth.orbit_camera(1920, 1080, az) for az in synth.ORBIT_AZIMUTHS]
+    return dict(name="paper-shaped: 512^3 f32 value noise (6 octaves) + 16 blobs (seed 1), 36 bricks "
+                     "(4x3x3), 1920x1080 perspective 60 deg orbit (8 views), step 0.5 voxel, "
+                     "early termination at alpha 0.99, radix-k composite 4x3x3",
+                vol=vol, tf=tf, part=dict(kind="grid", grid=(4, 3, 3)), cams=cams, step=0.5,
+                ert=0.99, schedule=(4, 3, 3), grid=(4, 3, 3))
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(prefix="clocks", suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on the host cores
+# --------------------------------------------------------------------------
+
+
+def oracle_rate(wl, budget_s: float = 12.0):
+    """Oracle samples/s on a centred crop of view 0 sized for ~budget_s of work."""
+    import oracle
+    vol, tf = wl["vol"], wl["tf"]
+    lo, hi = float(vol.min()), float(vol.max())
+    boxes = oracle.grid_partition(vol.shape[::-1], wl["grid"])
+    cam = wl["cams"][0]
+    W, H = cam["width"], cam["height"]
+    cores = os.cpu_count() or 1
+
+    def run(w, h):
+        x0, y0 = (W - w) // 2, (H - h) // 2
+        t = time.perf_counter()
+        r = oracle.render(vol, boxes, tf, lo, hi, cam, wl["step"], wl["ert"], crop=(x0, y0, w, h),
+                          threads=cores)
+        return r["nsamples"], time.perf_counter() - t
+
+    n, dt = run(min(W, 64), min(H, 64))
+    rate = n / max(dt, 1e-6)
+    target = rate * budget_s
+    side = 64
+    while side < max(W, H) and (n / (64 * 64)) * (2 * side) ** 2 < target:
+        side *= 2
+    w, h = min(W, side), min(H, side)
+    n, dt = run(w, h)
+    return dict(value=n / dt, unit=UNIT, cores=cores, kind="oracle",
+                sample="centred %dx%d crop of view 0 (%d samples, %.1f s, FP64, %d threads)"
+                       % (w, h, n, dt, cores)), n, dt
+
+
+def run_reference(a):
+    """The oracle as the reference arm: each step a bounded crop of the view."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = workload(a.workload)
+    vol, tf = wl["vol"], wl["tf"]
+    lo, hi = float(vol.min()), float(vol.max())
+    boxes = oracle.grid_partition(vol.shape[::-1], wl["grid"])
+    cores = os.cpu_count() or 1
+    crop = 48
+
+    def step(i):
+        cam = wl["cams"][i % len(wl["cams"])]
+        W, H = cam["width"], cam["height"]
+        w, h = min(W, crop), min(H, crop)
+        r = oracle.render(vol, boxes, tf, lo, hi, cam, wl["step"], wl["ert"],
+                          crop=((W - w) // 2, (H - h) // 2, w, h), threads=cores)
+        return r["nsamples"]
+
+    for i in range(a.warmup):
+        step(i)
+    t = time.perf_counter()
+    n = sum(step(a.warmup + i) for i in range(a.steps))
+    dt = time.perf_counter() - t
+    v = n / dt
+    line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=0, steps=a.steps,
+                warmup=a.warmup, ms_per_step=dt / a.steps * 1e3, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=wl["name"], sample="centred %dx%d crop per step" % (crop, crop)),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=cores, kind="oracle",
+                                  sample="%d steps of a centred %dx%d crop, FP64, %d threads"
+                                         % (a.steps, crop, crop, cores)),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    from paper_2501_01628_gb300 import vr
+
+    wl = workload(a.workload)
+    vol, tf = wl["vol"], wl["tf"]
+    lo, hi = float(vol.min()), float(vol.max())
+    cams = wl["cams"]
+    ctx = vr.vr_create(local)
+    v = vr.vr_volume_create(ctx, vol, "f32", wl["part"])
+    vr.vr_set_transfer_function(ctx, tf, lo, hi)
+    vr.vr_set_render_params(ctx, wl["step"], wl["ert"])
+    vr.vr_set_composite_schedule(ctx, wl["schedule"])
+    W, H = cams[0]["width"], cams[0]["height"]
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # executed samples per view (untimed, counting launch variant)
+    counts = []
+    rect_px = []
+    vr.vr_set_count_samples(ctx, True)
+    for cam in cams:
+        vr.vr_set_camera(ctx, cam)
+        vr.vr_render_frame(ctx, v, out)
+        counts.append(vr.vr_get_sample_count(ctx))
+        _, rects = vr.vr_plan_view(vol.shape[::-1], wl["part"], cam)
+        rect_px.append(int(sum(int(r[2]) * int(r[3]) for r in rects)))
+    vr.vr_set_count_samples(ctx, False)
+    views = [(rank + world * i) % len(cams) for i in range(a.warmup + a.steps)]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for i in range(a.warmup):
+        vr.vr_set_camera(ctx, cams[views[i]])
+        vr.vr_render_frame(ctx, v, out)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region -----------------------------------
+    timed_views = views[a.warmup:]
+    clocks = ClockSampler(local)
+    clocks.start()
+    vr.vr_get_kernel_timing(ctx)
+    vr.vr_set_kernel_timing(ctx, True)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for vi in timed_views:
+        vr.vr_set_camera(ctx, cams[vi])
+        vr.vr_render_frame(ctx, v, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    kt = vr.vr_get_kernel_timing(ctx)
+    vr.vr_set_kernel_timing(ctx, False)
+
+    # ---- end to end through the C ABI with a pinned host image -----------
+    host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for vi in timed_views:
+        vr.vr_set_camera(ctx, cams[vi])
+        vr.vr_render_frame(ctx, v, host)  # copies the frame to host and waits
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    samples = float(sum(counts[vi] for vi in timed_views))
+    tensor = torch.tensor([ms, e2e_s, samples], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        mx = tensor[:2].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tensor[2:].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms, e2e_s, samples = float(mx[0]), float(mx[1]), float(sm[0])
+    vr.vr_volume_release(v)
+    vr.vr_destroy(ctx)
+    if rank != 0:
+        return
+
+    K = a.steps
+    value = samples / (ms / 1e3)
+    frames = world * K / (ms / 1e3)
+    per_frame_samples = samples / (world * K)
+    march_ms = kt["march_ms"] / max(1, kt["march_launches"])
+    comp_ms = kt["composite_ms"] / max(1, kt["composite_launches"])
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "of measured" if hbm else "of fallback"
+    hbm = hbm or 6800.0
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    march_tflops = FLOPS_PER_SAMPLE * per_frame_samples / (march_ms / 1e3) / 1e12
+    mean_rect = sum(rect_px[vi] for vi in timed_views) / len(timed_views)
+    comp_bytes = (mean_rect + W * H) * 16
+    comp_gbs = comp_bytes / (comp_ms / 1e3) / 1e9
+    vol_bytes = vol.size * 4
+    march_hbm_gbs = (vol_bytes + mean_rect * 16) / (march_ms / 1e3) / 1e9
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        cpu, _, _ = oracle_rate(wl)
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=K, warmup=a.warmup,
+        ms_per_step=ms / K, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32", data="synthetic",
+        config=dict(workload=wl["name"], volume=list(vol.shape[::-1]), bricks=len(counts) and
+                    int(np.prod(wl["grid"])), image=[W, H], views=len(cams),
+                    l2="inputs larger than L2: %.0f MB of bricked volume vs 129 MB L2" % (vol_bytes / 1e6)
+                    if vol_bytes > 129e6 else "small workload fits in L2",
+                    parallelism="replicas over views" if world > 1 else "1 GPU"),
+        frames_per_s=frames,
+        samples_per_frame=per_frame_samples,
+        gpu_launches=2 * K,
+        clocks=clk,
+        roofline=dict(bound="alu", kernel="march", achieved=march_tflops, peak=fp32_peak, unit="TFLOP/s",
+                      frac=march_tflops / fp32_peak, traffic=None,
+                      note="FP32 %d flops/sample x executed samples / mean march launch; peak = 152 SMs x "
+                           "128 lanes x 2 x %.0f MHz (derived)" % (FLOPS_PER_SAMPLE, sm_max)),
+        roofline_hbm=dict(march=dict(achieved=march_hbm_gbs, peak=hbm, unit="GB/s", frac=march_hbm_gbs / hbm,
+                                     note="compulsory bytes (volume once + partial writes) / march time, %s"
+                                          % hbm_src),
+                          composite=dict(achieved=comp_gbs, peak=hbm, unit="GB/s", frac=comp_gbs / hbm,
+                                         note="partial reads + image write / composite time, %s" % hbm_src)),
+        kernel_ms=dict(march=march_ms, composite=comp_ms),
+        cpu_baseline=cpu,
+        e2e=dict(value=samples / e2e_s, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=W * H * 16,
+                 note="vr_render_frame into pinned host memory: render + 33 MB device-to-host copy + wait "
+                      "per frame; the per-step host inputs are the camera (kernel parameters)"),
+    )
+    print(json.dumps(line))
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

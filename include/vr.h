@@ -1,0 +1,206 @@
+/*
+ * vr.h -- C ABI of libvr, a GB300 (sm_103a) data-parallel volume renderer.
+ *
+ * The library renders one scalar volume split into bricks that all live on
+ * one GPU. Each brick stands in for one rank of the paper's cluster
+ * (arXiv:2501.01628, Sec. 2.2: the data is spatially distributed across ranks,
+ * each rank getting a share, possibly uneven; Sec. 4: several data parts are
+ * recombined per GPU). A frame is rendered in two steps that follow the paper's
+ * statement of the problem (Sec. 3: a collective render call retires pixels into
+ * a framebuffer that ends up in one place; Sec. 4: processes "render and
+ * composite images"):
+ *   1. per-brick emission-absorption ray marching on a global sample lattice,
+ *      giving one partial RGBA image per brick (vr_render_partials), and
+ *   2. sort-last compositing of the partials with the "over" operator in
+ *      front-to-back visibility order (vr_composite).
+ * The paper gives no rendering formula; the library implements the standard
+ * emission-absorption model (Max 1995) with these definitions:
+ *   - world box [0,Nx/Nmax]x[0,Ny/Nmax]x[0,Nz/Nmax], voxel centres at (i+.5)/Nmax;
+ *   - samples t_k = t_in + (k+1/2) dt, dt = step_voxels/Nmax, while t_k < t_out,
+ *     [t_in,t_out) the ray's interval in the whole-volume box (t_in >= 0);
+ *   - sample k belongs to the brick whose voxel box holds the cell
+ *     clamp(floor(p*Nmax), 0, N-1) of its position p;
+ *   - trilinear reconstruction with clamp-to-edge; 1D RGBA table lookup with
+ *     linear interpolation over [vmin, vmax]; per-sample opacity = table alpha;
+ *   - per brick: C += T*alpha*rgb, T *= (1-alpha) from C=0, T=1; the partial is
+ *     (C, 1-T) (premultiplied colour); optional early termination per brick
+ *     when T <= 1 - ert_alpha;
+ *   - composite: C <- C + (1-A) C_b, A <- A + (1-A) A_b, bricks front to back.
+ *
+ * Conventions for every call:
+ *   - Return value: VR_OK or an error code; no call aborts or exits. The text
+ *     of the last error of a context is available from vr_last_error().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Device work is asynchronous on that stream unless stated.
+ *   - Pointers named *_dev are device pointers owned by the caller; the
+ *     library never frees them. Objects created by vr_*_create / vr_render_*
+ *     are owned by the library until the matching release call.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Images are row-major [height][width][4] float32 RGBA, row 0 at the
+ *     bottom of the view (pixel (px,py) has its centre at ((px+.5)/W, (py+.5)/H)
+ *     of the image plane).
+ */
+#ifndef VR_H
+#define VR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vr_ctx_s *vr_ctx;
+typedef struct vr_volume_s *vr_volume;
+typedef struct vr_frame_s *vr_frame;
+
+typedef enum {
+    VR_OK = 0,
+    VR_ERR_ARG = 1,     /* invalid argument (bad dims, partition that does not tile, ...) */
+    VR_ERR_OOM = 2,     /* device or host allocation failed */
+    VR_ERR_CUDA = 3,    /* a CUDA runtime call failed; see vr_last_error */
+    VR_ERR_STATE = 4,   /* call out of order (no camera / transfer function yet, ...) */
+    VR_ERR_TIMEOUT = 5, /* a bounded device-side wait gave up */
+    VR_ERR_BOUNDS = 6   /* a device-side index check failed */
+} vr_status;
+
+typedef enum { VR_F32 = 0, VR_BF16 = 1, VR_F16 = 2 } vr_dtype;
+
+typedef enum { VR_PART_GRID = 0, VR_PART_KD = 1, VR_PART_BOXES = 2 } vr_partition_kind;
+
+/* Camera (Sec. 2.1: primary rays start at the virtual camera).
+ * Basis f = dir/|dir|, r = normalise(up x f), u = f x r.
+ * Orthographic (ortho != 0): ray origin eye + ((px+.5)/W-.5) ortho_w r
+ *   + ((py+.5)/H-.5) ortho_h u, direction f.
+ * Perspective: origin eye, direction normalise(f + sx r + sy u) with
+ *   sy = ((py+.5)/H*2-1) tan(fovy/2), sx = ((px+.5)/W*2-1) tan(fovy/2) W/H. */
+typedef struct {
+    int ortho;
+    double eye[3], dir[3], up[3];
+    double fovy_deg, ortho_w, ortho_h;
+    int width, height;
+} vr_camera;
+
+/* Brick partition of the volume (Sec. 2.2 spatial distribution; Sec. 4 uneven
+ * shares and several parts per GPU).
+ *   VR_PART_GRID : grid[0] x grid[1] x grid[2] bricks, boundaries floor(N j/g),
+ *                  brick id (bz*gy + by)*gx + bx.
+ *   VR_PART_KD   : n_bricks leaves; repeatedly the leaf with the most voxels
+ *                  (ties: lowest id) is cut across its longest axis (ties:
+ *                  x, y, z) at lo + round(cut_fracs[j]*extent), clamped so both
+ *                  halves are non-empty; the low half keeps the id, the high
+ *                  half gets the next id. cut_fracs holds n_bricks-1 values.
+ *   VR_PART_BOXES: n_bricks half-open voxel boxes (lo x,y,z, hi x,y,z) that
+ *                  tile the volume and can be separated by axis-aligned cuts
+ *                  (needed for a visibility order); otherwise VR_ERR_ARG.
+ * At most VR_MAX_BRICKS bricks. */
+#define VR_MAX_BRICKS 128
+typedef struct {
+    int kind;
+    int grid[3];
+    int n_bricks;
+    const double *cut_fracs;
+    const int *boxes;
+} vr_partition;
+
+/* ---- host-only planning (no GPU needed) -------------------------------- */
+
+/* Bricks that `part` produces for a dims[0] x dims[1] x dims[2] volume: their
+ * count and, if `boxes` is not NULL, their voxel boxes (n x 6 ints). Fails with
+ * VR_ERR_ARG for an invalid description or boxes that do not tile the volume
+ * with axis-aligned cuts. */
+vr_status vr_partition_boxes(const int dims[3], const vr_partition *part, int *n_bricks, int *boxes);
+/* Per-view plan of a partitioned volume: front-to-back brick order (n ids,
+ * from a traversal of the partition's kd tree towards the eye, or along the view
+ * direction for orthographic cameras; ties resolved low side first) and the
+ * conservative screen rectangle of each brick (n x 4: x0, y0, w, h; w = h = 0
+ * when the brick cannot be seen). Either output may be NULL. */
+vr_status vr_plan_view(const int dims[3], const vr_partition *part, const vr_camera *cam, int *order,
+                       int *rects);
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `cuda_device`. */
+vr_status vr_create(int cuda_device, vr_ctx *out);
+/* Destroy a context; its volumes and frames must have been released. Waits for
+ * the device. */
+vr_status vr_destroy(vr_ctx ctx);
+const char *vr_status_string(vr_status s);
+/* Text of the last error of `ctx` ("" if none); valid until the next call. */
+const char *vr_last_error(vr_ctx ctx);
+/* Wait for `stream` and report any device-side error word set by a kernel. */
+vr_status vr_sync(vr_ctx ctx, void *stream);
+
+/* ---- volume (the distributed World of Sec. 3, all bricks on this GPU) ---- */
+
+/* Create a volume of dims[0] x dims[1] x dims[2] voxels (x fastest) from the
+ * float32 array `src` (host memory if src_on_device == 0, else device memory;
+ * not retained) and pack it into brick-major storage of type `storage`
+ * (float32, or bfloat16 / float16 rounded to nearest even) with a one-voxel
+ * halo per brick holding the neighbouring (edge-clamped) voxels. The packing
+ * runs on `stream` and is complete when this call returns. */
+vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage,
+                           const vr_partition *part, const float *src, int src_on_device,
+                           void *stream, vr_volume *out);
+vr_status vr_volume_release(vr_volume vol);
+/* Number of bricks, their voxel boxes (n x 6 ints, may be NULL) and the bytes
+ * of brick storage in device memory (may be NULL). */
+vr_status vr_volume_info(vr_volume vol, int *n_bricks, int *boxes, long long *storage_bytes);
+/* Copy brick `brick`'s haloed storage, (bx+2)(by+2)(bz+2) elements x fastest,
+ * into host memory `dst` of `bytes` bytes (synchronous). For tests. */
+vr_status vr_volume_read_brick(vr_volume vol, int brick, void *dst, size_t bytes);
+
+/* ---- renderer state --------------------------------------------------- */
+
+/* Transfer function: 2 <= n <= 1024 RGBA entries (entry i at u = i/(n-1)), scalar range
+ * [vmin, vmax] with vmax > vmin. `rgba` is host memory (on_device == 0) or
+ * device memory; it is copied, synchronously. */
+vr_status vr_set_transfer_function(vr_ctx ctx, const float *rgba, int n, float vmin, float vmax,
+                                   int on_device);
+vr_status vr_set_camera(vr_ctx ctx, const vr_camera *cam);
+/* step_voxels > 0 (default 0.5); ert_alpha in (0,1) enables early ray
+ * termination per brick, >= 1 disables it (default 1). */
+vr_status vr_set_render_params(vr_ctx ctx, float step_voxels, float ert_alpha);
+/* Compositing association tree: n_factors factors whose product equals the
+ * brick count (radix-k rounds: groups of factors[0] consecutive partials in
+ * visibility order are combined first, then groups of factors[1] of those, ...).
+ * n_factors == 0 selects direct k-way compositing. At most 8 factors. */
+vr_status vr_set_composite_schedule(vr_ctx ctx, int n_factors, const int *factors);
+/* When on, every march launch also counts executed samples (see
+ * vr_get_sample_count). Off by default. */
+vr_status vr_set_count_samples(vr_ctx ctx, int on);
+/* Samples counted since the last call (synchronises the context's device). */
+vr_status vr_get_sample_count(vr_ctx ctx, long long *count);
+
+/* When on, the library records a CUDA event pair on the launching stream
+ * around each of its march and composite kernel launches. Off by default. */
+vr_status vr_set_kernel_timing(vr_ctx ctx, int on);
+/* Summed device time (ms) and launch count of the march and composite kernels
+ * recorded since the last call (waits for the recorded events). Any output may
+ * be NULL. */
+vr_status vr_get_kernel_timing(vr_ctx ctx, double *march_ms, long long *march_launches,
+                               double *composite_ms, long long *composite_launches);
+
+/* ---- rendering --------------------------------------------------------- */
+
+/* Step 1: march every brick, producing one partial RGBA32F image per brick
+ * over the brick's screen footprint rectangle. The frame (partials, rectangles,
+ * visibility order) belongs to the library until vr_frame_release. */
+vr_status vr_render_partials(vr_ctx ctx, vr_volume vol, vr_frame *out, void *stream);
+/* Frame layout: rects n x 4 (x0, y0, w, h) per brick id, order n brick ids front
+ * to back (either may be NULL). */
+vr_status vr_frame_info(vr_frame fr, int *n_bricks, int *rects, int *order);
+/* Device pointer to brick `brick`'s partial: h rows of w float4 (RGBA). */
+vr_status vr_frame_partial(vr_frame fr, int brick, const float **dev_ptr);
+/* Step 2: composite the frame's partials front to back with the context's
+ * schedule into out_rgba (device memory if out_on_device, else host memory; a
+ * host output makes the call synchronous). */
+vr_status vr_composite(vr_ctx ctx, vr_frame fr, float *out_rgba, int out_on_device, void *stream);
+vr_status vr_frame_release(vr_frame fr);
+/* Steps 1 + 2 with a context-owned frame (no allocation once warm). */
+vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on_device,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VR_H */

@@ -1,0 +1,964 @@
+// vr_host.cpp -- host runtime of libvr: contexts, brick partitions and their
+// kd visibility trees, per-view footprint rectangles and launch tables, and the
+// C ABI declared in include/vr.h.
+//
+// Sec. 2.2 of arXiv:2501.01628: data is spatially distributed over ranks
+// (here: bricks on one GPU); the distribution may be uneven (Sec. 4).
+// Sec. 3: rendering is one collective call whose image ends up in one
+// framebuffer; the world is distributed and updated locally.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vr_internal.h"
+
+using namespace vr;
+
+namespace {
+
+struct KdNode {
+    int axis = -1;  // -1: leaf
+    int cut = 0;    // voxel plane
+    int child[2] = {-1, -1};
+    int brick = -1;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct vr_frame_s {
+    vr_ctx ctx = nullptr;
+    int nb = 0;
+    int W = 0, H = 0;
+    std::vector<int> rects;        // nb x 4
+    std::vector<int> order;        // nb
+    std::vector<long long> poff;   // nb, float4 units
+    long long total_px = 0;
+    float4 *d_part = nullptr;
+    long long cap_px = 0;
+    bool owned_by_ctx = false;
+};
+
+struct vr_ctx_s {
+    int device = 0;
+    std::string last_error;
+    float4 *d_tf = nullptr;
+    int ntf = 0;
+    int tf_cap = 0;
+    float vmin = 0.f, vmax = 1.f;
+    bool has_tf = false;
+    vr_camera cam{};
+    bool has_cam = false;
+    float step = 0.5f;
+    float ert_alpha = 1.0f;
+    std::vector<int> factors;
+    unsigned long long *d_counter = nullptr;
+    bool count_samples = false;
+    vr_frame_s frame;              // context-owned frame for vr_render_frame
+    float4 *d_img = nullptr;       // staging for host outputs
+    long long img_cap = 0;
+    int live_objects = 0;
+    // kernel timing (vr_set_kernel_timing)
+    bool timing = false;
+    struct Timed {
+        cudaEvent_t a, b;
+        int kind;  // 0 march, 1 composite
+    };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+struct vr_volume_s {
+    vr_ctx ctx = nullptr;
+    int dims[3] = {0, 0, 0};
+    vr_dtype dtype = VR_F32;
+    std::vector<int> boxes;        // nb x 6
+    std::vector<long long> base;   // element offsets
+    std::vector<KdNode> tree;      // node 0 = root
+    void *d_data = nullptr;
+    long long bytes = 0;
+};
+
+namespace {
+
+size_t elem_size(vr_dtype t) { return t == VR_F32 ? 4 : 2; }
+
+vr_status fail(vr_ctx ctx, vr_status s, const std::string &msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return s;
+}
+
+vr_status cuda_fail(vr_ctx ctx, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA, m);
+}
+
+#define VR_CUDA(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+int nmax3(const int d[3]) { return std::max(d[0], std::max(d[1], d[2])); }
+
+// ---- partitions -----------------------------------------------------------
+
+bool grid_boxes(const int dims[3], const int g[3], std::vector<int> &boxes)
+{
+    for (int a = 0; a < 3; ++a)
+        if (g[a] < 1 || g[a] > dims[a]) return false;
+    boxes.clear();
+    for (int bz = 0; bz < g[2]; ++bz)
+        for (int by = 0; by < g[1]; ++by)
+            for (int bx = 0; bx < g[0]; ++bx) {
+                const int b[3] = {bx, by, bz};
+                int lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = static_cast<int>((static_cast<long long>(dims[a]) * b[a]) / g[a]);
+                    hi[a] = static_cast<int>((static_cast<long long>(dims[a]) * (b[a] + 1)) / g[a]);
+                }
+                boxes.insert(boxes.end(), {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]});
+            }
+    return true;
+}
+
+bool kd_boxes(const int dims[3], int n, const double *u, std::vector<int> &boxes)
+{
+    if (n < 1 || (n > 1 && !u)) return false;
+    boxes.assign(6 * static_cast<size_t>(n), 0);
+    boxes[3] = dims[0];
+    boxes[4] = dims[1];
+    boxes[5] = dims[2];
+    for (int count = 1; count < n; ++count) {
+        int best = 0;
+        long long bestv = -1;
+        for (int l = 0; l < count; ++l) {
+            const int *b = &boxes[6 * l];
+            long long v = static_cast<long long>(b[3] - b[0]) * (b[4] - b[1]) * (b[5] - b[2]);
+            if (v > bestv) {
+                bestv = v;
+                best = l;
+            }
+        }
+        int *b = &boxes[6 * best];
+        int axis = 0;
+        for (int a = 1; a < 3; ++a)
+            if (b[3 + a] - b[a] > b[3 + axis] - b[axis]) axis = a;
+        const int ext = b[3 + axis] - b[axis];
+        if (ext < 2 || !(u[count - 1] >= 0.0 && u[count - 1] <= 1.0)) return false;
+        int cut = b[axis] + static_cast<int>(std::floor(u[count - 1] * ext + 0.5));
+        cut = std::min(std::max(cut, b[axis] + 1), b[3 + axis] - 1);
+        int *nbx = &boxes[6 * count];
+        std::memcpy(nbx, b, 6 * sizeof(int));
+        b[3 + axis] = cut;
+        nbx[axis] = cut;
+    }
+    return true;
+}
+
+// Builds a kd tree over `ids` (boxes inside `region`) by finding axis-aligned
+// planes that separate the boxes; fails if the boxes do not tile the region or
+// admit no such plane. Front-to-back order is then a tree traversal.
+bool build_tree(const std::vector<int> &boxes, std::vector<int> ids, const int region[6],
+                std::vector<KdNode> &tree, int &node_out)
+{
+    node_out = static_cast<int>(tree.size());
+    tree.emplace_back();
+    if (ids.size() == 1) {
+        const int *b = &boxes[6 * ids[0]];
+        for (int i = 0; i < 6; ++i)
+            if (b[i] != region[i]) return false;
+        tree[node_out].brick = ids[0];
+        return true;
+    }
+    for (int axis = 0; axis < 3; ++axis) {
+        std::vector<int> cands;
+        for (int id : ids) cands.push_back(boxes[6 * id + axis]);
+        std::sort(cands.begin(), cands.end());
+        cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+        for (int c : cands) {
+            if (c <= region[axis] || c >= region[3 + axis]) continue;
+            std::vector<int> lo_ids, hi_ids;
+            bool ok = true;
+            for (int id : ids) {
+                const int *b = &boxes[6 * id];
+                if (b[3 + axis] <= c) lo_ids.push_back(id);
+                else if (b[axis] >= c) hi_ids.push_back(id);
+                else {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!ok || lo_ids.empty() || hi_ids.empty()) continue;
+            int rlo[6], rhi[6];
+            std::memcpy(rlo, region, sizeof(rlo));
+            std::memcpy(rhi, region, sizeof(rhi));
+            rlo[3 + axis] = c;
+            rhi[axis] = c;
+            int a = -1, b = -1;
+            if (!build_tree(boxes, lo_ids, rlo, tree, a)) return false;
+            if (!build_tree(boxes, hi_ids, rhi, tree, b)) return false;
+            tree[node_out].axis = axis;
+            tree[node_out].cut = c;
+            tree[node_out].child[0] = a;
+            tree[node_out].child[1] = b;
+            return true;
+        }
+    }
+    return false;
+}
+
+void visibility_order(const std::vector<KdNode> &tree, int node, const vr_camera &cam, double nmax,
+                      std::vector<int> &out)
+{
+    const KdNode &n = tree[node];
+    if (n.axis < 0) {
+        out.push_back(n.brick);
+        return;
+    }
+    bool low_first;
+    if (cam.ortho) low_first = cam.dir[n.axis] >= 0.0;
+    else low_first = cam.eye[n.axis] * nmax <= static_cast<double>(n.cut);
+    visibility_order(tree, n.child[low_first ? 0 : 1], cam, nmax, out);
+    visibility_order(tree, n.child[low_first ? 1 : 0], cam, nmax, out);
+}
+
+struct Basis {
+    double f[3], r[3], u[3];
+    double tanx, tany;
+};
+
+void normalize(double v[3])
+{
+    const double l = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= l;
+    v[1] /= l;
+    v[2] /= l;
+}
+
+void cross(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+bool make_basis(const vr_camera &c, Basis &B)
+{
+    for (int i = 0; i < 3; ++i) B.f[i] = c.dir[i];
+    if (B.f[0] == 0 && B.f[1] == 0 && B.f[2] == 0) return false;
+    normalize(B.f);
+    cross(c.up, B.f, B.r);
+    if (B.r[0] == 0 && B.r[1] == 0 && B.r[2] == 0) return false;
+    normalize(B.r);
+    cross(B.f, B.r, B.u);
+    const double th = std::tan(c.fovy_deg * M_PI / 360.0);
+    B.tany = th;
+    B.tanx = th * static_cast<double>(c.width) / c.height;
+    return true;
+}
+
+// Conservative pixel rectangle of a brick's projected bounding box (+1 px).
+void footprint(const vr_camera &c, const Basis &B, const int box[6], double nmax, int rect[4])
+{
+    const int W = c.width, H = c.height;
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    int behind = 0;
+    for (int k = 0; k < 8; ++k) {
+        double q[3], v[3];
+        for (int a = 0; a < 3; ++a) {
+            q[a] = ((k >> a) & 1 ? box[3 + a] : box[a]) / nmax;
+            v[a] = q[a] - c.eye[a];
+        }
+        const double vr = v[0] * B.r[0] + v[1] * B.r[1] + v[2] * B.r[2];
+        const double vu = v[0] * B.u[0] + v[1] * B.u[1] + v[2] * B.u[2];
+        double x, y;
+        if (c.ortho) {
+            x = (vr / c.ortho_w + 0.5) * W - 0.5;
+            y = (vu / c.ortho_h + 0.5) * H - 0.5;
+        } else {
+            const double z = v[0] * B.f[0] + v[1] * B.f[1] + v[2] * B.f[2];
+            if (z <= 1e-9) {
+                ++behind;
+                continue;
+            }
+            x = (vr / (z * B.tanx) + 1.0) * 0.5 * W - 0.5;
+            y = (vu / (z * B.tany) + 1.0) * 0.5 * H - 0.5;
+        }
+        xmin = std::min(xmin, x);
+        xmax = std::max(xmax, x);
+        ymin = std::min(ymin, y);
+        ymax = std::max(ymax, y);
+    }
+    if (behind == 8) {
+        rect[0] = rect[1] = rect[2] = rect[3] = 0;
+        return;
+    }
+    if (behind > 0) {
+        rect[0] = 0;
+        rect[1] = 0;
+        rect[2] = W;
+        rect[3] = H;
+        return;
+    }
+    const double x0 = std::max(0.0, std::floor(xmin) - 1.0), x1 = std::min(W - 1.0, std::ceil(xmax) + 1.0);
+    const double y0 = std::max(0.0, std::floor(ymin) - 1.0), y1 = std::min(H - 1.0, std::ceil(ymax) + 1.0);
+    if (x1 < x0 || y1 < y0) {
+        rect[0] = rect[1] = rect[2] = rect[3] = 0;
+        return;
+    }
+    rect[0] = static_cast<int>(x0);
+    rect[1] = static_cast<int>(y0);
+    rect[2] = static_cast<int>(x1 - x0) + 1;
+    rect[3] = static_cast<int>(y1 - y0) + 1;
+}
+
+// Boxes + kd tree of a partition description; false (with a reason) if invalid.
+bool partition_plan(const int dims[3], const vr_partition *part, std::vector<int> &boxes,
+                    std::vector<KdNode> &tree, const char **why)
+{
+    *why = "invalid partition description";
+    if (!dims || !part) return false;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (1 << 16)) {
+            *why = "bad volume dims";
+            return false;
+        }
+    bool ok = false;
+    switch (part->kind) {
+    case VR_PART_GRID: ok = grid_boxes(dims, part->grid, boxes); break;
+    case VR_PART_KD: ok = kd_boxes(dims, part->n_bricks, part->cut_fracs, boxes); break;
+    case VR_PART_BOXES:
+        if (part->boxes && part->n_bricks >= 1 && part->n_bricks <= kMaxBricks) {
+            boxes.assign(part->boxes, part->boxes + 6 * static_cast<size_t>(part->n_bricks));
+            ok = true;
+        }
+        break;
+    default: break;
+    }
+    if (!ok) return false;
+    const int nb = static_cast<int>(boxes.size() / 6);
+    if (nb > kMaxBricks) {
+        *why = "too many bricks";
+        return false;
+    }
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < 3; ++a) {
+            const int lo = boxes[6 * b + a], hi = boxes[6 * b + 3 + a];
+            if (lo < 0 || hi > dims[a] || lo >= hi) {
+                *why = "brick box out of range";
+                return false;
+            }
+        }
+    std::vector<int> ids(nb);
+    for (int b = 0; b < nb; ++b) ids[b] = b;
+    const int region[6] = {0, 0, 0, dims[0], dims[1], dims[2]};
+    int root = -1;
+    tree.clear();
+    if (!build_tree(boxes, ids, region, tree, root)) {
+        *why = "bricks do not tile the volume with axis-aligned cuts";
+        return false;
+    }
+    return true;
+}
+
+bool camera_valid(const vr_camera *cam)
+{
+    if (!cam || cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768) return false;
+    if (cam->ortho ? !(cam->ortho_w > 0 && cam->ortho_h > 0) : !(cam->fovy_deg > 0 && cam->fovy_deg < 180))
+        return false;
+    Basis B;
+    return make_basis(*cam, B);
+}
+
+vr_status ensure_frame(vr_ctx ctx, vr_frame_s &fr, long long px)
+{
+    if (px <= fr.cap_px) return VR_OK;
+    const long long want = std::max(px, fr.cap_px + fr.cap_px / 4);
+    if (fr.d_part) cudaFree(fr.d_part);
+    fr.d_part = nullptr;
+    fr.cap_px = 0;
+    VR_CUDA(ctx, cudaMalloc(&fr.d_part, static_cast<size_t>(want) * sizeof(float4)));
+    fr.cap_px = want;
+    return VR_OK;
+}
+
+// Per-view setup (host, tiny): visibility order, footprints, launch table.
+vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &mp)
+{
+    if (!ctx->has_cam) return fail(ctx, VR_ERR_STATE, "no camera set");
+    if (!ctx->has_tf) return fail(ctx, VR_ERR_STATE, "no transfer function set");
+    const vr_camera &c = ctx->cam;
+    Basis B;
+    if (!make_basis(c, B)) return fail(ctx, VR_ERR_ARG, "degenerate camera basis");
+    const int nb = static_cast<int>(vol->boxes.size() / 6);
+    const double nmax = nmax3(vol->dims);
+    fr.ctx = ctx;
+    fr.nb = nb;
+    fr.W = c.width;
+    fr.H = c.height;
+    fr.rects.assign(4 * nb, 0);
+    fr.poff.assign(nb, 0);
+    fr.order.clear();
+    visibility_order(vol->tree, 0, c, nmax, fr.order);
+    long long px = 0;
+    int items = 0;
+    std::memset(&mp, 0, sizeof(mp));
+    for (int b = 0; b < nb; ++b) {
+        int *r = &fr.rects[4 * b];
+        footprint(c, B, &vol->boxes[6 * b], nmax, r);
+        fr.poff[b] = px;
+        px += static_cast<long long>(r[2]) * r[3];
+        px = (px + 7) & ~7LL;  // 128-byte aligned partial starts
+        BrickLaunch &L = mp.b[b];
+        const int *bx = &vol->boxes[6 * b];
+        for (int a = 0; a < 3; ++a) {
+            L.lo[a] = bx[a];
+            L.hi[a] = bx[3 + a];
+            L.own_lo[a] = bx[a] == 0 ? -INFINITY : static_cast<float>(bx[a]);
+            L.own_hi[a] = bx[3 + a] == vol->dims[a] ? INFINITY : static_cast<float>(bx[3 + a]);
+        }
+        L.sx = bx[3] - bx[0] + 2;
+        L.sy = bx[4] - bx[1] + 2;
+        L.base = vol->base[b];
+        std::memcpy(L.rect, r, sizeof(L.rect));
+        L.poff = fr.poff[b];
+        L.item_begin = items;
+        L.tiles_x = (r[2] + kTileW - 1) / kTileW;
+        const int tiles_y = (r[3] + kTileH - 1) / kTileH;
+        items += L.tiles_x * tiles_y;
+    }
+    fr.total_px = px;
+    for (int a = 0; a < 3; ++a) {
+        mp.eye[a] = static_cast<float>(c.eye[a]);
+        mp.r[a] = static_cast<float>(B.r[a]);
+        mp.u[a] = static_cast<float>(B.u[a]);
+        mp.f[a] = static_cast<float>(B.f[a]);
+        mp.N[a] = static_cast<float>(vol->dims[a]);
+    }
+    mp.tanx = static_cast<float>(B.tanx);
+    mp.tany = static_cast<float>(B.tany);
+    mp.ow = static_cast<float>(c.ortho_w);
+    mp.oh = static_cast<float>(c.ortho_h);
+    mp.ortho = c.ortho ? 1 : 0;
+    mp.W = c.width;
+    mp.H = c.height;
+    mp.nmax = static_cast<float>(nmax);
+    const double dt = static_cast<double>(ctx->step) / nmax;
+    mp.dt = static_cast<float>(dt);
+    mp.inv_dt = static_cast<float>(1.0 / dt);
+    mp.ert_T = ctx->ert_alpha < 1.0f ? static_cast<float>(1.0 - static_cast<double>(ctx->ert_alpha)) : -1.0f;
+    mp.vmin = ctx->vmin;
+    mp.inv_range = static_cast<float>(1.0 / (static_cast<double>(ctx->vmax) - ctx->vmin));
+    mp.ntf = ctx->ntf;
+    mp.tf = ctx->d_tf;
+    mp.data = vol->d_data;
+    mp.sample_counter = ctx->count_samples ? ctx->d_counter : nullptr;
+    mp.nb = nb;
+    mp.n_items = items;
+    return VR_OK;
+}
+
+cudaEvent_t pooled_event(vr_ctx ctx)
+{
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records the start event of a timed launch; returns the index or -1.
+int timing_begin(vr_ctx ctx, int kind, cudaStream_t s)
+{
+    if (!ctx->timing) return -1;
+    cudaEvent_t a = pooled_event(ctx), b = pooled_event(ctx);
+    if (!a || !b || cudaEventRecord(a, s) != cudaSuccess) {
+        if (a) ctx->event_pool.push_back(a);
+        if (b) ctx->event_pool.push_back(b);
+        return -1;
+    }
+    ctx->timed.push_back({a, b, kind});
+    return static_cast<int>(ctx->timed.size()) - 1;
+}
+
+void timing_end(vr_ctx ctx, int idx, cudaStream_t s)
+{
+    if (idx >= 0) cudaEventRecord(ctx->timed[idx].b, s);
+}
+
+vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s)
+{
+    static thread_local MarchParams mp;  // ~12 KB: keep off the stack
+    vr_status st = prepare_frame(ctx, vol, fr, mp);
+    if (st != VR_OK) return st;
+    st = ensure_frame(ctx, fr, std::max(fr.total_px, 1LL));
+    if (st != VR_OK) return st;
+    mp.partials = fr.d_part;
+    const int t = timing_begin(ctx, 0, s);
+    VR_CUDA(ctx, launch_march(mp, vol->dtype, s));
+    timing_end(ctx, t, s);
+    return VR_OK;
+}
+
+vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s)
+{
+    static thread_local CompositeParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.W = fr.W;
+    cp.H = fr.H;
+    cp.nb = fr.nb;
+    const int nf = static_cast<int>(ctx->factors.size());
+    long long prod = 1;
+    for (int k : ctx->factors) prod *= k;
+    const bool radix = nf > 0 && prod == fr.nb;
+    if (nf > 0 && !radix)
+        return fail(ctx, VR_ERR_ARG, "composite schedule factors do not multiply to the brick count");
+    cp.n_levels = radix ? nf : 1;
+    for (int j = 0; j < fr.nb; ++j) {
+        cp.order[j] = fr.order[j];
+        int c = 0;
+        if (radix) {
+            long long m = j + 1;
+            while (c < nf - 1 && m % ctx->factors[c] == 0) {
+                m /= ctx->factors[c];
+                ++c;
+            }
+        }
+        cp.carry[j] = static_cast<unsigned char>(c);
+    }
+    for (int b = 0; b < fr.nb; ++b) {
+        std::memcpy(cp.rect[b], &fr.rects[4 * b], 4 * sizeof(int));
+        cp.poff[b] = fr.poff[b];
+    }
+    cp.partials = fr.d_part;
+    cp.out = out;
+    const int t = timing_begin(ctx, 1, s);
+    VR_CUDA(ctx, launch_composite(cp, s));
+    timing_end(ctx, t, s);
+    return VR_OK;
+}
+
+vr_status composite_to(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s)
+{
+    if (!out) return fail(ctx, VR_ERR_ARG, "null output");
+    const long long px = static_cast<long long>(fr.W) * fr.H;
+    if (out_on_device) return composite(ctx, fr, reinterpret_cast<float4 *>(out), s);
+    if (px > ctx->img_cap) {
+        if (ctx->d_img) cudaFree(ctx->d_img);
+        ctx->d_img = nullptr;
+        ctx->img_cap = 0;
+        VR_CUDA(ctx, cudaMalloc(&ctx->d_img, static_cast<size_t>(px) * sizeof(float4)));
+        ctx->img_cap = px;
+    }
+    vr_status st = composite(ctx, fr, ctx->d_img, s);
+    if (st != VR_OK) return st;
+    VR_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_img, static_cast<size_t>(px) * sizeof(float4),
+                                 cudaMemcpyDeviceToHost, s));
+    VR_CUDA(ctx, cudaStreamSynchronize(s));
+    return VR_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *vr_status_string(vr_status s)
+{
+    switch (s) {
+    case VR_OK: return "ok";
+    case VR_ERR_ARG: return "invalid argument";
+    case VR_ERR_OOM: return "out of memory";
+    case VR_ERR_CUDA: return "CUDA error";
+    case VR_ERR_STATE: return "invalid state";
+    case VR_ERR_TIMEOUT: return "device wait timed out";
+    case VR_ERR_BOUNDS: return "device index check failed";
+    }
+    return "unknown status";
+}
+
+const char *vr_last_error(vr_ctx ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+vr_status vr_partition_boxes(const int dims[3], const vr_partition *part, int *n_bricks, int *boxes)
+{
+    std::vector<int> bx;
+    std::vector<KdNode> tree;
+    const char *why = nullptr;
+    if (!partition_plan(dims, part, bx, tree, &why)) return VR_ERR_ARG;
+    if (n_bricks) *n_bricks = static_cast<int>(bx.size() / 6);
+    if (boxes) std::memcpy(boxes, bx.data(), bx.size() * sizeof(int));
+    return VR_OK;
+}
+
+vr_status vr_plan_view(const int dims[3], const vr_partition *part, const vr_camera *cam, int *order, int *rects)
+{
+    std::vector<int> bx;
+    std::vector<KdNode> tree;
+    const char *why = nullptr;
+    if (!partition_plan(dims, part, bx, tree, &why) || !camera_valid(cam)) return VR_ERR_ARG;
+    Basis B;
+    make_basis(*cam, B);
+    const double nmax = nmax3(dims);
+    const int nb = static_cast<int>(bx.size() / 6);
+    if (order) {
+        std::vector<int> o;
+        visibility_order(tree, 0, *cam, nmax, o);
+        std::memcpy(order, o.data(), o.size() * sizeof(int));
+    }
+    if (rects)
+        for (int b = 0; b < nb; ++b) footprint(*cam, B, &bx[6 * b], nmax, rects + 4 * b);
+    return VR_OK;
+}
+
+vr_status vr_create(int cuda_device, vr_ctx *out)
+{
+    if (!out) return VR_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n) {
+        cudaGetLastError();
+        return VR_ERR_ARG;
+    }
+    vr_ctx ctx = new (std::nothrow) vr_ctx_s;
+    if (!ctx) return VR_ERR_OOM;
+    ctx->device = cuda_device;
+    DeviceGuard g(cuda_device);
+    if (!g.ok || cudaMalloc(&ctx->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_counter, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return VR_ERR_CUDA;
+    }
+    ctx->frame.owned_by_ctx = true;
+    *out = ctx;
+    return VR_OK;
+}
+
+vr_status vr_destroy(vr_ctx ctx)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (ctx->live_objects != 0) return fail(ctx, VR_ERR_STATE, "volumes or frames still alive");
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(ctx->d_tf);
+    cudaFree(ctx->d_counter);
+    cudaFree(ctx->frame.d_part);
+    cudaFree(ctx->d_img);
+    for (auto &t : ctx->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    delete ctx;
+    return VR_OK;
+}
+
+vr_status vr_set_kernel_timing(vr_ctx ctx, int on)
+{
+    if (!ctx) return VR_ERR_ARG;
+    ctx->timing = on != 0;
+    return VR_OK;
+}
+
+vr_status vr_get_kernel_timing(vr_ctx ctx, double *march_ms, long long *march_launches, double *composite_ms,
+                               long long *composite_launches)
+{
+    if (!ctx) return VR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    double ms[2] = {0, 0};
+    long long n[2] = {0, 0};
+    vr_status st = VR_OK;
+    for (auto &t : ctx->timed) {
+        float e = 0.f;
+        if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&e, t.a, t.b) == cudaSuccess) {
+            ms[t.kind] += e;
+            n[t.kind] += 1;
+        } else {
+            cudaGetLastError();
+            st = fail(ctx, VR_ERR_CUDA, "kernel timing event failed");
+        }
+        ctx->event_pool.push_back(t.a);
+        ctx->event_pool.push_back(t.b);
+    }
+    ctx->timed.clear();
+    if (march_ms) *march_ms = ms[0];
+    if (march_launches) *march_launches = n[0];
+    if (composite_ms) *composite_ms = ms[1];
+    if (composite_launches) *composite_launches = n[1];
+    return st;
+}
+
+vr_status vr_sync(vr_ctx ctx, void *stream)
+{
+    if (!ctx) return VR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    VR_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return VR_OK;
+}
+
+vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, const vr_partition *part,
+                           const float *src, int src_on_device, void *stream, vr_volume *out)
+{
+    if (!ctx || !out) return VR_ERR_ARG;
+    *out = nullptr;
+    if (!dims || !part || !src) return fail(ctx, VR_ERR_ARG, "null argument");
+    if (storage != VR_F32 && storage != VR_BF16 && storage != VR_F16)
+        return fail(ctx, VR_ERR_ARG, "unknown storage type");
+    std::unique_ptr<vr_volume_s> vol(new (std::nothrow) vr_volume_s);
+    if (!vol) return VR_ERR_OOM;
+    vol->ctx = ctx;
+    std::memcpy(vol->dims, dims, sizeof(vol->dims));
+    vol->dtype = storage;
+    const char *why = nullptr;
+    if (!partition_plan(dims, part, vol->boxes, vol->tree, &why)) return fail(ctx, VR_ERR_ARG, why);
+    const int nb = static_cast<int>(vol->boxes.size() / 6);
+
+    // brick-major haloed storage, each brick 256-byte aligned
+    const size_t es = elem_size(storage);
+    long long off_bytes = 0;
+    vol->base.resize(nb);
+    for (int b = 0; b < nb; ++b) {
+        const int *bx = &vol->boxes[6 * b];
+        const long long n = static_cast<long long>(bx[3] - bx[0] + 2) * (bx[4] - bx[1] + 2) * (bx[5] - bx[2] + 2);
+        vol->base[b] = off_bytes / static_cast<long long>(es);
+        off_bytes += n * static_cast<long long>(es);
+        off_bytes = (off_bytes + 255) & ~255LL;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VR_CUDA(ctx, cudaMalloc(&vol->d_data, static_cast<size_t>(off_bytes)));
+    vol->bytes = off_bytes;
+    const float *dsrc = src;
+    float *tmp = nullptr;
+    const size_t nvox = static_cast<size_t>(dims[0]) * dims[1] * dims[2];
+    if (!src_on_device) {
+        cudaError_t e = cudaMalloc(&tmp, nvox * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, nvox * sizeof(float), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            cudaFree(vol->d_data);
+            return cuda_fail(ctx, e, "volume upload");
+        }
+        dsrc = tmp;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        const int *bx = &vol->boxes[6 * b];
+        PackParams pp;
+        pp.src = dsrc;
+        pp.dst = static_cast<char *>(vol->d_data) + vol->base[b] * static_cast<long long>(es);
+        for (int a = 0; a < 3; ++a) {
+            pp.N[a] = dims[a];
+            pp.lo[a] = bx[a];
+            pp.s[a] = bx[3 + a] - bx[a] + 2;
+        }
+        pp.count = static_cast<long long>(pp.s[0]) * pp.s[1] * pp.s[2];
+        e = launch_pack(pp, storage, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        cudaFree(vol->d_data);
+        return cuda_fail(ctx, e, "volume pack");
+    }
+    ctx->live_objects++;
+    *out = vol.release();
+    return VR_OK;
+}
+
+vr_status vr_volume_release(vr_volume vol)
+{
+    if (!vol) return VR_ERR_ARG;
+    DeviceGuard g(vol->ctx->device);
+    cudaFree(vol->d_data);
+    vol->ctx->live_objects--;
+    delete vol;
+    return VR_OK;
+}
+
+vr_status vr_volume_info(vr_volume vol, int *n_bricks, int *boxes, long long *storage_bytes)
+{
+    if (!vol) return VR_ERR_ARG;
+    if (n_bricks) *n_bricks = static_cast<int>(vol->boxes.size() / 6);
+    if (boxes) std::memcpy(boxes, vol->boxes.data(), vol->boxes.size() * sizeof(int));
+    if (storage_bytes) *storage_bytes = vol->bytes;
+    return VR_OK;
+}
+
+vr_status vr_volume_read_brick(vr_volume vol, int brick, void *dst, size_t bytes)
+{
+    if (!vol || !dst) return VR_ERR_ARG;
+    const int nb = static_cast<int>(vol->boxes.size() / 6);
+    if (brick < 0 || brick >= nb) return fail(vol->ctx, VR_ERR_ARG, "brick index out of range");
+    const int *bx = &vol->boxes[6 * brick];
+    const size_t n = static_cast<size_t>(bx[3] - bx[0] + 2) * (bx[4] - bx[1] + 2) * (bx[5] - bx[2] + 2) *
+                     elem_size(vol->dtype);
+    if (bytes < n) return fail(vol->ctx, VR_ERR_ARG, "destination too small");
+    DeviceGuard g(vol->ctx->device);
+    VR_CUDA(vol->ctx, cudaMemcpy(dst, static_cast<const char *>(vol->d_data) +
+                                          vol->base[brick] * static_cast<long long>(elem_size(vol->dtype)),
+                                 n, cudaMemcpyDeviceToHost));
+    return VR_OK;
+}
+
+vr_status vr_set_transfer_function(vr_ctx ctx, const float *rgba, int n, float vmin, float vmax, int on_device)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (!rgba || n < 2 || n > 1024 || !(vmax > vmin) || !std::isfinite(vmin) || !std::isfinite(vmax))
+        return fail(ctx, VR_ERR_ARG, "bad transfer function");
+    DeviceGuard g(ctx->device);
+    if (n > ctx->tf_cap) {
+        cudaFree(ctx->d_tf);
+        ctx->d_tf = nullptr;
+        ctx->tf_cap = 0;
+        ctx->has_tf = false;
+        VR_CUDA(ctx, cudaMalloc(&ctx->d_tf, static_cast<size_t>(n) * sizeof(float4)));
+        ctx->tf_cap = n;
+    }
+    VR_CUDA(ctx, cudaMemcpy(ctx->d_tf, rgba, static_cast<size_t>(n) * sizeof(float4),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    ctx->ntf = n;
+    ctx->vmin = vmin;
+    ctx->vmax = vmax;
+    ctx->has_tf = true;
+    return VR_OK;
+}
+
+vr_status vr_set_camera(vr_ctx ctx, const vr_camera *cam)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (!camera_valid(cam)) return fail(ctx, VR_ERR_ARG, "bad camera (size, extent, field of view or basis)");
+    ctx->cam = *cam;
+    ctx->has_cam = true;
+    return VR_OK;
+}
+
+vr_status vr_set_render_params(vr_ctx ctx, float step_voxels, float ert_alpha)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (!(step_voxels > 0.0f) || !(ert_alpha > 0.0f)) return fail(ctx, VR_ERR_ARG, "bad render params");
+    ctx->step = step_voxels;
+    ctx->ert_alpha = ert_alpha;
+    return VR_OK;
+}
+
+vr_status vr_set_composite_schedule(vr_ctx ctx, int n_factors, const int *factors)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (n_factors < 0 || n_factors > kMaxFactors || (n_factors > 0 && !factors))
+        return fail(ctx, VR_ERR_ARG, "bad schedule");
+    for (int i = 0; i < n_factors; ++i)
+        if (factors[i] < 1) return fail(ctx, VR_ERR_ARG, "bad schedule factor");
+    ctx->factors.assign(factors, factors + n_factors);
+    return VR_OK;
+}
+
+vr_status vr_set_count_samples(vr_ctx ctx, int on)
+{
+    if (!ctx) return VR_ERR_ARG;
+    ctx->count_samples = on != 0;
+    return VR_OK;
+}
+
+vr_status vr_get_sample_count(vr_ctx ctx, long long *count)
+{
+    if (!ctx || !count) return VR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    unsigned long long v = 0;
+    VR_CUDA(ctx, cudaDeviceSynchronize());
+    VR_CUDA(ctx, cudaMemcpy(&v, ctx->d_counter, sizeof(v), cudaMemcpyDeviceToHost));
+    VR_CUDA(ctx, cudaMemset(ctx->d_counter, 0, sizeof(v)));
+    *count = static_cast<long long>(v);
+    return VR_OK;
+}
+
+vr_status vr_render_partials(vr_ctx ctx, vr_volume vol, vr_frame *out, void *stream)
+{
+    if (!ctx || !vol || !out) return VR_ERR_ARG;
+    *out = nullptr;
+    if (vol->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume belongs to another context");
+    std::unique_ptr<vr_frame_s> fr(new (std::nothrow) vr_frame_s);
+    if (!fr) return VR_ERR_OOM;
+    DeviceGuard g(ctx->device);
+    vr_status st = march(ctx, vol, *fr, static_cast<cudaStream_t>(stream));
+    if (st != VR_OK) {
+        cudaFree(fr->d_part);
+        return st;
+    }
+    ctx->live_objects++;
+    *out = fr.release();
+    return VR_OK;
+}
+
+vr_status vr_frame_info(vr_frame fr, int *n_bricks, int *rects, int *order)
+{
+    if (!fr) return VR_ERR_ARG;
+    if (n_bricks) *n_bricks = fr->nb;
+    if (rects) std::memcpy(rects, fr->rects.data(), fr->rects.size() * sizeof(int));
+    if (order) std::memcpy(order, fr->order.data(), fr->order.size() * sizeof(int));
+    return VR_OK;
+}
+
+vr_status vr_frame_partial(vr_frame fr, int brick, const float **dev_ptr)
+{
+    if (!fr || !dev_ptr || brick < 0 || brick >= fr->nb) return VR_ERR_ARG;
+    *dev_ptr = reinterpret_cast<const float *>(fr->d_part + fr->poff[brick]);
+    return VR_OK;
+}
+
+vr_status vr_composite(vr_ctx ctx, vr_frame fr, float *out_rgba, int out_on_device, void *stream)
+{
+    if (!ctx || !fr) return VR_ERR_ARG;
+    if (fr->ctx != ctx) return fail(ctx, VR_ERR_ARG, "frame belongs to another context");
+    DeviceGuard g(ctx->device);
+    return composite_to(ctx, *fr, out_rgba, out_on_device, static_cast<cudaStream_t>(stream));
+}
+
+vr_status vr_frame_release(vr_frame fr)
+{
+    if (!fr || fr->owned_by_ctx) return VR_ERR_ARG;
+    DeviceGuard g(fr->ctx->device);
+    cudaFree(fr->d_part);
+    fr->ctx->live_objects--;
+    delete fr;
+    return VR_OK;
+}
+
+vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on_device, void *stream)
+{
+    if (!ctx || !vol) return VR_ERR_ARG;
+    if (vol->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume belongs to another context");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    vr_status st = march(ctx, vol, ctx->frame, s);
+    if (st != VR_OK) return st;
+    return composite_to(ctx, ctx->frame, out_rgba, out_on_device, s);
+}
+
+}  // extern "C"

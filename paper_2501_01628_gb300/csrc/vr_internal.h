@@ -1,0 +1,86 @@
+// vr_internal.h -- structures shared by the host runtime (vr_host.cpp) and the
+// CUDA kernels (vr_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/vr.h"
+
+namespace vr {
+
+constexpr int kMaxBricks = VR_MAX_BRICKS;
+constexpr int kMaxFactors = 8;
+
+// March tile: 16 x 8 pixels per 128-thread block, four 8 x 4 warp packets.
+constexpr int kTileW = 16;
+constexpr int kTileH = 8;
+// Composite tile: 32 x 8 pixels per 256-thread block.
+constexpr int kCompW = 32;
+constexpr int kCompH = 8;
+
+// Per-brick data of one frame, as the march kernel needs it.
+struct BrickLaunch {
+    int lo[3], hi[3];   // voxel box, half-open
+    float own_lo[3];    // ownership bounds in voxel units (-inf / +inf on volume faces)
+    float own_hi[3];
+    int sx, sy;         // haloed brick extents in x and y (elements)
+    long long base;     // element offset of the brick's haloed storage
+    int rect[4];        // x0, y0, w, h of the footprint rectangle
+    long long poff;     // float4 offset of the brick's partial
+    int item_begin;     // first work item (tile) of this brick
+    int tiles_x;        // tiles per rectangle row
+};
+
+// Everything one march launch needs; passed by value as the kernel parameter.
+struct MarchParams {
+    // camera, all FP32 (basis computed on the host in FP64)
+    float eye[3], r[3], u[3], f[3];
+    float tanx, tany;   // perspective: tan(fovy/2)*W/H, tan(fovy/2)
+    float ow, oh;       // orthographic image-plane extent
+    int ortho;
+    int W, H;
+    // volume
+    float nmax;         // voxels per world unit
+    float N[3];         // volume extent in voxels
+    float dt, inv_dt;   // sample spacing (world units) and its inverse
+    float ert_T;        // terminate a brick when T <= ert_T (negative: never)
+    // classification
+    float vmin, inv_range;
+    int ntf;
+    const float4 *tf;   // ntf entries
+    const void *data;   // brick storage
+    float4 *partials;   // partial pool
+    unsigned long long *sample_counter;  // non-null: count executed samples
+    int nb;
+    int n_items;
+    BrickLaunch b[kMaxBricks];
+};
+
+struct CompositeParams {
+    int W, H;
+    int nb;
+    int n_levels;                     // 1 = direct
+    int order[kMaxBricks];            // brick ids front to back
+    unsigned char carry[kMaxBricks];  // levels to carry after position j
+    int rect[kMaxBricks][4];          // by brick id
+    long long poff[kMaxBricks];       // by brick id
+    const float4 *partials;
+    float4 *out;
+};
+
+struct PackParams {
+    const float *src;
+    void *dst;
+    int N[3];
+    int lo[3];
+    int s[3];       // haloed extents
+    long long count;
+};
+
+// Launchers (vr_kernels.cu). They return the launch's cudaError_t.
+cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s);
+cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s);
+cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s);
+
+}  // namespace vr

@@ -1,0 +1,378 @@
+"""Thin ctypes binding of libvr (include/vr.h): same call names, argument
+marshalling only. Every step of the rendering path runs in the library's CUDA
+kernels; this module never computes pixels itself and raises if the library is
+missing.
+
+Arrays: volumes are [Nz, Ny, Nx] float32 (numpy or torch, host or CUDA);
+images are [H, W, 4] float32 torch tensors (CUDA for device output, pinned or
+pageable CPU for host output). Streams default to torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvr.so")
+_lock = threading.Lock()
+_lib = None
+
+VR_OK, VR_ERR_ARG, VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_STATE, VR_ERR_TIMEOUT, VR_ERR_BOUNDS = range(7)
+VR_F32, VR_BF16, VR_F16 = 0, 1, 2
+VR_PART_GRID, VR_PART_KD, VR_PART_BOXES = 0, 1, 2
+VR_MAX_BRICKS = 128
+DTYPES = {"f32": VR_F32, "bf16": VR_BF16, "f16": VR_F16}
+
+# Every function the header declares (checked by the CPU test-suite).
+EXPORTS = (
+    "vr_create", "vr_destroy", "vr_status_string", "vr_last_error", "vr_sync",
+    "vr_volume_create", "vr_volume_release", "vr_volume_info", "vr_volume_read_brick",
+    "vr_set_transfer_function", "vr_set_camera", "vr_set_render_params",
+    "vr_set_composite_schedule", "vr_set_count_samples", "vr_get_sample_count",
+    "vr_render_partials", "vr_frame_info", "vr_frame_partial", "vr_composite",
+    "vr_frame_release", "vr_render_frame", "vr_partition_boxes", "vr_plan_view",
+    "vr_set_kernel_timing", "vr_get_kernel_timing",
+)
+
+
+class VrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class vr_camera(ctypes.Structure):
+    _fields_ = [("ortho", ctypes.c_int), ("eye", ctypes.c_double * 3),
+                ("dir", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("fovy_deg", ctypes.c_double), ("ortho_w", ctypes.c_double),
+                ("ortho_h", ctypes.c_double), ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class vr_partition(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("grid", ctypes.c_int * 3), ("n_bricks", ctypes.c_int),
+                ("cut_fracs", ctypes.c_void_p), ("boxes", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIG = {
+    "vr_create": (_I, [_I, ctypes.POINTER(_P)]),
+    "vr_destroy": (_I, [_P]),
+    "vr_status_string": (ctypes.c_char_p, [_I]),
+    "vr_last_error": (ctypes.c_char_p, [_P]),
+    "vr_sync": (_I, [_P, _P]),
+    "vr_volume_create": (_I, [_P, _P, _I, ctypes.POINTER(vr_partition), _P, _I, _P, ctypes.POINTER(_P)]),
+    "vr_volume_release": (_I, [_P]),
+    "vr_volume_info": (_I, [_P, _P, _P, _P]),
+    "vr_volume_read_brick": (_I, [_P, _I, _P, ctypes.c_size_t]),
+    "vr_set_transfer_function": (_I, [_P, _P, _I, ctypes.c_float, ctypes.c_float, _I]),
+    "vr_set_camera": (_I, [_P, ctypes.POINTER(vr_camera)]),
+    "vr_set_render_params": (_I, [_P, ctypes.c_float, ctypes.c_float]),
+    "vr_set_composite_schedule": (_I, [_P, _I, _P]),
+    "vr_set_count_samples": (_I, [_P, _I]),
+    "vr_get_sample_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "vr_render_partials": (_I, [_P, _P, ctypes.POINTER(_P), _P]),
+    "vr_frame_info": (_I, [_P, _P, _P, _P]),
+    "vr_frame_partial": (_I, [_P, _I, ctypes.POINTER(_P)]),
+    "vr_composite": (_I, [_P, _P, _P, _I, _P]),
+    "vr_frame_release": (_I, [_P]),
+    "vr_render_frame": (_I, [_P, _P, _P, _I, _P]),
+    "vr_set_kernel_timing": (_I, [_P, _I]),
+    "vr_get_kernel_timing": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
+    "vr_plan_view": (_I, [_P, ctypes.POINTER(vr_partition), ctypes.POINTER(vr_camera), _P, _P]),
+}
+
+
+def lib():
+    """Load libvr.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libvr.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIG.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, ctx=None, what: str = ""):
+    if status != VR_OK:
+        L = lib()
+        msg = L.vr_status_string(status).decode()
+        if ctx is not None:
+            detail = L.vr_last_error(ctx).decode()
+            if detail:
+                msg += ": " + detail
+        raise VrError(status, "%s failed: %s" % (what, msg))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr_and_loc(x):
+    """(pointer, on_device, keepalive) of a contiguous float32 array/tensor."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return x.data_ptr(), int(x.is_cuda), x
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, 0, a
+
+
+# --------------------------------------------------------------------------
+# Calls (same names as the C ABI)
+# --------------------------------------------------------------------------
+
+
+def vr_create(cuda_device: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib().vr_create(int(cuda_device), ctypes.byref(h)), None, "vr_create")
+    return h
+
+
+def vr_destroy(ctx):
+    _check(lib().vr_destroy(ctx), ctx, "vr_destroy")
+
+
+def vr_sync(ctx, stream=None):
+    _check(lib().vr_sync(ctx, _stream(stream)), ctx, "vr_sync")
+
+
+def make_partition(kind: str = "grid", grid=(1, 1, 1), n_bricks: int = 1, cut_fracs=None,
+                   boxes=None):
+    """Returns (vr_partition, keepalive)."""
+    p = vr_partition()
+    keep = []
+    if kind == "grid":
+        p.kind = VR_PART_GRID
+        p.grid[:] = [int(g) for g in grid]
+    elif kind == "kd":
+        p.kind = VR_PART_KD
+        p.n_bricks = int(n_bricks)
+        u = np.ascontiguousarray(cut_fracs if cut_fracs is not None else [], dtype=np.float64)
+        keep.append(u)
+        p.cut_fracs = u.ctypes.data if u.size else None
+    elif kind == "boxes":
+        p.kind = VR_PART_BOXES
+        b = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 6)
+        keep.append(b)
+        p.n_bricks = b.shape[0]
+        p.boxes = b.ctypes.data
+    else:
+        raise ValueError(kind)
+    return p, keep
+
+
+def vr_partition_boxes(dims, partition=None):
+    """Host-only: (n, 6) voxel boxes of a partition description for dims (x, y, z)."""
+    d = (ctypes.c_int * 3)(*[int(v) for v in dims])
+    part, keep = make_partition(**(partition or {}))
+    n = ctypes.c_int()
+    _check(lib().vr_partition_boxes(d, ctypes.byref(part), ctypes.byref(n), None), None,
+           "vr_partition_boxes")
+    boxes = np.zeros((n.value, 6), np.int32)
+    _check(lib().vr_partition_boxes(d, ctypes.byref(part), None, boxes.ctypes.data), None,
+           "vr_partition_boxes")
+    return boxes
+
+
+def vr_plan_view(dims, partition, cam: dict):
+    """Host-only: (order (n,), rects (n, 4)) of a partitioned volume for a camera."""
+    boxes = vr_partition_boxes(dims, partition)
+    d = (ctypes.c_int * 3)(*[int(v) for v in dims])
+    part, keep = make_partition(**(partition or {}))
+    c = camera_struct(cam)
+    order = np.zeros(boxes.shape[0], np.int32)
+    rects = np.zeros((boxes.shape[0], 4), np.int32)
+    _check(lib().vr_plan_view(d, ctypes.byref(part), ctypes.byref(c), order.ctypes.data,
+                              rects.ctypes.data), None, "vr_plan_view")
+    return order, rects
+
+
+def vr_volume_create(ctx, volume, storage: str = "f32", partition=None, stream=None):
+    """volume: [Nz, Ny, Nx] float32 (numpy / torch, host or CUDA).
+    partition: dict for make_partition (default: one brick)."""
+    ptr, on_dev, keep = _ptr_and_loc(volume)
+    if getattr(keep, "dtype", None) is not None and str(keep.dtype) not in ("float32", "torch.float32"):
+        raise TypeError("volume must be float32")
+    nz, ny, nx = tuple(keep.shape)
+    dims = (ctypes.c_int * 3)(nx, ny, nz)
+    part, pk = make_partition(**(partition or {}))
+    h = ctypes.c_void_p()
+    _check(lib().vr_volume_create(ctx, dims, DTYPES[storage], ctypes.byref(part), ptr, on_dev,
+                                  _stream(stream), ctypes.byref(h)), ctx, "vr_volume_create")
+    return h
+
+
+def vr_volume_release(vol):
+    _check(lib().vr_volume_release(vol), None, "vr_volume_release")
+
+
+def vr_volume_info(vol):
+    n = ctypes.c_int()
+    _check(lib().vr_volume_info(vol, ctypes.byref(n), None, None), None, "vr_volume_info")
+    boxes = np.zeros((n.value, 6), np.int32)
+    nbytes = ctypes.c_longlong()
+    _check(lib().vr_volume_info(vol, None, boxes.ctypes.data, ctypes.byref(nbytes)), None,
+           "vr_volume_info")
+    return boxes, int(nbytes.value)
+
+
+def vr_volume_read_brick(vol, brick: int, storage: str = "f32"):
+    boxes, _ = vr_volume_info(vol)
+    b = boxes[brick]
+    shape = (b[5] - b[2] + 2, b[4] - b[1] + 2, b[3] - b[0] + 2)
+    out = np.zeros(shape, np.float32 if storage == "f32" else np.uint16)
+    _check(lib().vr_volume_read_brick(vol, int(brick), out.ctypes.data, out.nbytes), None,
+           "vr_volume_read_brick")
+    return out
+
+
+def vr_set_transfer_function(ctx, rgba, vmin: float, vmax: float):
+    ptr, on_dev, keep = _ptr_and_loc(rgba)
+    n = int(keep.shape[0])
+    _check(lib().vr_set_transfer_function(ctx, ptr, n, float(vmin), float(vmax), on_dev), ctx,
+           "vr_set_transfer_function")
+
+
+def camera_struct(cam: dict) -> vr_camera:
+    c = vr_camera()
+    c.ortho = int(cam["ortho"])
+    for k in ("eye", "dir", "up"):
+        getattr(c, k)[:] = [float(v) for v in cam[k]]
+    c.fovy_deg = float(cam.get("fovy_deg", 0.0))
+    c.ortho_w = float(cam.get("ortho_w", 0.0))
+    c.ortho_h = float(cam.get("ortho_h", 0.0))
+    c.width = int(cam["width"])
+    c.height = int(cam["height"])
+    return c
+
+
+def vr_set_camera(ctx, cam: dict):
+    c = camera_struct(cam)
+    _check(lib().vr_set_camera(ctx, ctypes.byref(c)), ctx, "vr_set_camera")
+
+
+def vr_set_render_params(ctx, step_voxels: float = 0.5, ert_alpha: float = 1.0):
+    _check(lib().vr_set_render_params(ctx, float(step_voxels), float(ert_alpha)), ctx,
+           "vr_set_render_params")
+
+
+def vr_set_composite_schedule(ctx, factors=()):
+    f = np.ascontiguousarray(list(factors), dtype=np.int32)
+    _check(lib().vr_set_composite_schedule(ctx, int(f.size), f.ctypes.data if f.size else None),
+           ctx, "vr_set_composite_schedule")
+
+
+def vr_set_count_samples(ctx, on: bool):
+    _check(lib().vr_set_count_samples(ctx, int(bool(on))), ctx, "vr_set_count_samples")
+
+
+def vr_get_sample_count(ctx) -> int:
+    v = ctypes.c_longlong()
+    _check(lib().vr_get_sample_count(ctx, ctypes.byref(v)), ctx, "vr_get_sample_count")
+    return int(v.value)
+
+
+def vr_set_kernel_timing(ctx, on: bool):
+    _check(lib().vr_set_kernel_timing(ctx, int(bool(on))), ctx, "vr_set_kernel_timing")
+
+
+def vr_get_kernel_timing(ctx):
+    """dict(march_ms, march_launches, composite_ms, composite_launches) since the last call."""
+    a, c = ctypes.c_double(), ctypes.c_double()
+    na, nc = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().vr_get_kernel_timing(ctx, ctypes.byref(a), ctypes.byref(na), ctypes.byref(c),
+                                      ctypes.byref(nc)), ctx, "vr_get_kernel_timing")
+    return dict(march_ms=a.value, march_launches=na.value, composite_ms=c.value,
+                composite_launches=nc.value)
+
+
+def vr_render_partials(ctx, vol, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().vr_render_partials(ctx, vol, ctypes.byref(h), _stream(stream)), ctx,
+           "vr_render_partials")
+    return h
+
+
+def vr_frame_info(frame):
+    n = ctypes.c_int()
+    _check(lib().vr_frame_info(frame, ctypes.byref(n), None, None), None, "vr_frame_info")
+    rects = np.zeros((n.value, 4), np.int32)
+    order = np.zeros(n.value, np.int32)
+    _check(lib().vr_frame_info(frame, None, rects.ctypes.data, order.ctypes.data), None,
+           "vr_frame_info")
+    return rects, order
+
+
+def vr_frame_partial(frame, brick: int):
+    """Device pointer (int) of brick's partial: rect h rows x w float4."""
+    p = ctypes.c_void_p()
+    _check(lib().vr_frame_partial(frame, int(brick), ctypes.byref(p)), None, "vr_frame_partial")
+    return int(p.value or 0)
+
+
+def vr_composite(ctx, frame, out, stream=None):
+    ptr, on_dev, _ = _ptr_and_loc(out)
+    _check(lib().vr_composite(ctx, frame, ptr, on_dev, _stream(stream)), ctx, "vr_composite")
+
+
+def vr_frame_release(frame):
+    _check(lib().vr_frame_release(frame), None, "vr_frame_release")
+
+
+def vr_render_frame(ctx, vol, out, stream=None):
+    ptr, on_dev, _ = _ptr_and_loc(out)
+    _check(lib().vr_render_frame(ctx, vol, ptr, on_dev, _stream(stream)), ctx, "vr_render_frame")
+
+
+# --------------------------------------------------------------------------
+# Convenience: torch views of a frame's partials (tests, debugging)
+# --------------------------------------------------------------------------
+
+
+def frame_partials_torch(frame):
+    """List of [h, w, 4] CUDA tensors (copies) of each brick's partial."""
+    import torch
+    rects, _ = vr_frame_info(frame)
+    out = []
+    for b, (x0, y0, w, h) in enumerate(rects):
+        if w * h == 0:
+            out.append(torch.zeros((int(h), int(w), 4), dtype=torch.float32, device="cuda"))
+            continue
+        view = _tensor_from_ptr(vr_frame_partial(frame, b), int(w * h * 4))
+        out.append(view.clone().reshape(int(h), int(w), 4))
+    return out
+
+
+class _CudaArray:
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = dict(shape=(n,), typestr="<f4", data=(ptr, False),
+                                             version=3, strides=None, stream=None)
+
+
+def _tensor_from_ptr(ptr: int, n: int):
+    """float32 CUDA tensor view of n elements at a device address owned by libvr."""
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, n), device="cuda")
