@@ -43,7 +43,7 @@ SMS, FP32_LANES = 152, 128
 def args_parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper", choices=["paper", "small"])
@@ -128,33 +128,26 @@ class ClockSampler:
 
 
 def oracle_rate(wl, budget_s: float = 12.0):
-    """Oracle samples/s on a centred crop of view 0 sized for ~budget_s of work."""
+    """Oracle samples/s over whole frames of successive views, until about
+    budget_s of host time is spent (every host core)."""
     import oracle
     vol, tf = wl["vol"], wl["tf"]
     lo, hi = float(vol.min()), float(vol.max())
     boxes = oracle.grid_partition(vol.shape[::-1], wl["grid"])
-    cam = wl["cams"][0]
-    W, H = cam["width"], cam["height"]
     cores = os.cpu_count() or 1
-
-    def run(w, h):
-        x0, y0 = (W - w) // 2, (H - h) // 2
-        t = time.perf_counter()
-        r = oracle.render(vol, boxes, tf, lo, hi, cam, wl["step"], wl["ert"], crop=(x0, y0, w, h),
-                          threads=cores)
-        return r["nsamples"], time.perf_counter() - t
-
-    n, dt = run(min(W, 64), min(H, 64))
-    rate = n / max(dt, 1e-6)
-    target = rate * budget_s
-    side = 64
-    while side < max(W, H) and (n / (64 * 64)) * (2 * side) ** 2 < target:
-        side *= 2
-    w, h = min(W, side), min(H, side)
-    n, dt = run(w, h)
+    n = 0
+    frames = 0
+    t = time.perf_counter()
+    while time.perf_counter() - t < budget_s and frames < 64:
+        cam = wl["cams"][frames % len(wl["cams"])]
+        n += oracle.render(vol, boxes, tf, lo, hi, cam, wl["step"], wl["ert"], threads=cores)["nsamples"]
+        frames += 1
+    dt = time.perf_counter() - t
+    W, H = wl["cams"][0]["width"], wl["cams"][0]["height"]
     return dict(value=n / dt, unit=UNIT, cores=cores, kind="oracle",
-                sample="centred %dx%d crop of view 0 (%d samples, %.1f s, FP64, %d threads)"
-                       % (w, h, n, dt, cores)), n, dt
+                frames_per_s=frames / dt,
+                sample="%d full %dx%d frames of successive orbit views (%d samples, %.1f s, FP64, %d threads)"
+                       % (frames, W, H, n, dt, cores)), n, dt
 
 
 def run_reference(a):

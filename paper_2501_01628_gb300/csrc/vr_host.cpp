@@ -100,6 +100,12 @@ struct vr_volume_s {
 namespace {
 
 size_t elem_size(vr_dtype t) { return t == VR_F32 ? 4 : 2; }
+// bytes of one xy-quad (four voxels) in device storage
+size_t quad_size(vr_dtype t) { return 4 * elem_size(t); }
+long long brick_quads(const int *bx)
+{
+    return static_cast<long long>(bx[3] - bx[0] + 1) * (bx[4] - bx[1] + 1) * (bx[5] - bx[2] + 2);
+}
 
 vr_status fail(vr_ctx ctx, vr_status s, const std::string &msg)
 {
@@ -468,8 +474,11 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
     mp.dt = static_cast<float>(dt);
     mp.inv_dt = static_cast<float>(1.0 / dt);
     mp.ert_T = ctx->ert_alpha < 1.0f ? static_cast<float>(1.0 - static_cast<double>(ctx->ert_alpha)) : -1.0f;
-    mp.vmin = ctx->vmin;
-    mp.inv_range = static_cast<float>(1.0 / (static_cast<double>(ctx->vmax) - ctx->vmin));
+    {
+        const double scale = (ctx->ntf - 1) / (static_cast<double>(ctx->vmax) - ctx->vmin);
+        mp.tf_scale = static_cast<float>(scale);
+        mp.tf_bias = static_cast<float>(-static_cast<double>(ctx->vmin) * scale);
+    }
     mp.ntf = ctx->ntf;
     mp.tf = ctx->d_tf;
     mp.data = vol->d_data;
@@ -739,15 +748,13 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
     if (!partition_plan(dims, part, vol->boxes, vol->tree, &why)) return fail(ctx, VR_ERR_ARG, why);
     const int nb = static_cast<int>(vol->boxes.size() / 6);
 
-    // brick-major haloed storage, each brick 256-byte aligned
-    const size_t es = elem_size(storage);
+    // brick-major haloed xy-quad storage, each brick 256-byte aligned
+    const size_t es = quad_size(storage);
     long long off_bytes = 0;
     vol->base.resize(nb);
     for (int b = 0; b < nb; ++b) {
-        const int *bx = &vol->boxes[6 * b];
-        const long long n = static_cast<long long>(bx[3] - bx[0] + 2) * (bx[4] - bx[1] + 2) * (bx[5] - bx[2] + 2);
         vol->base[b] = off_bytes / static_cast<long long>(es);
-        off_bytes += n * static_cast<long long>(es);
+        off_bytes += brick_quads(&vol->boxes[6 * b]) * static_cast<long long>(es);
         off_bytes = (off_bytes + 255) & ~255LL;
     }
     DeviceGuard g(ctx->device);
@@ -778,7 +785,6 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
             pp.lo[a] = bx[a];
             pp.s[a] = bx[3 + a] - bx[a] + 2;
         }
-        pp.count = static_cast<long long>(pp.s[0]) * pp.s[1] * pp.s[2];
         e = launch_pack(pp, storage, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -817,13 +823,28 @@ vr_status vr_volume_read_brick(vr_volume vol, int brick, void *dst, size_t bytes
     const int nb = static_cast<int>(vol->boxes.size() / 6);
     if (brick < 0 || brick >= nb) return fail(vol->ctx, VR_ERR_ARG, "brick index out of range");
     const int *bx = &vol->boxes[6 * brick];
-    const size_t n = static_cast<size_t>(bx[3] - bx[0] + 2) * (bx[4] - bx[1] + 2) * (bx[5] - bx[2] + 2) *
-                     elem_size(vol->dtype);
+    const int sx = bx[3] - bx[0] + 2, sy = bx[4] - bx[1] + 2, sz = bx[5] - bx[2] + 2;
+    const size_t es = elem_size(vol->dtype);
+    const size_t n = static_cast<size_t>(sx) * sy * sz * es;
     if (bytes < n) return fail(vol->ctx, VR_ERR_ARG, "destination too small");
+    const long long nq = brick_quads(bx);
+    std::vector<unsigned char> q(static_cast<size_t>(nq) * 4 * es);
     DeviceGuard g(vol->ctx->device);
-    VR_CUDA(vol->ctx, cudaMemcpy(dst, static_cast<const char *>(vol->d_data) +
-                                          vol->base[brick] * static_cast<long long>(elem_size(vol->dtype)),
-                                 n, cudaMemcpyDeviceToHost));
+    VR_CUDA(vol->ctx, cudaMemcpy(q.data(), static_cast<const char *>(vol->d_data) +
+                                               vol->base[brick] * static_cast<long long>(4 * es),
+                                 q.size(), cudaMemcpyDeviceToHost));
+    // voxel (i,j,k) is component (i==sx-1) + 2*(j==sy-1) of quad (min(i,sx-2), min(j,sy-2), k)
+    const int qx = sx - 1, qy = sy - 1;
+    unsigned char *out = static_cast<unsigned char *>(dst);
+    for (int k = 0; k < sz; ++k)
+        for (int j = 0; j < sy; ++j)
+            for (int i = 0; i < sx; ++i) {
+                const int ii = std::min(i, qx - 1), jj = std::min(j, qy - 1);
+                const int c = (i == sx - 1 ? 1 : 0) + (j == sy - 1 ? 2 : 0);
+                const size_t src = ((static_cast<size_t>(k) * qy + jj) * qx + ii) * 4 + c;
+                const size_t o = (static_cast<size_t>(k) * sy + j) * sx + i;
+                std::memcpy(out + o * es, q.data() + src * es, es);
+            }
     return VR_OK;
 }
 
@@ -838,11 +859,23 @@ vr_status vr_set_transfer_function(vr_ctx ctx, const float *rgba, int n, float v
         ctx->d_tf = nullptr;
         ctx->tf_cap = 0;
         ctx->has_tf = false;
-        VR_CUDA(ctx, cudaMalloc(&ctx->d_tf, static_cast<size_t>(n) * sizeof(float4)));
+        VR_CUDA(ctx, cudaMalloc(&ctx->d_tf, 2 * static_cast<size_t>(n) * sizeof(float4)));
         ctx->tf_cap = n;
     }
-    VR_CUDA(ctx, cudaMemcpy(ctx->d_tf, rgba, static_cast<size_t>(n) * sizeof(float4),
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    // device table: (T[i], T[i+1] - T[i]) pairs in float32, last difference 0
+    std::vector<float> t(4 * static_cast<size_t>(n)), pairs(8 * static_cast<size_t>(n));
+    if (on_device)
+        VR_CUDA(ctx, cudaMemcpy(t.data(), rgba, t.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(t.data(), rgba, t.size() * sizeof(float));
+    for (int i = 0; i < n; ++i)
+        for (int c = 0; c < 4; ++c) {
+            const float a = t[4 * i + c];
+            const float b = i + 1 < n ? t[4 * (i + 1) + c] : a;
+            pairs[8 * i + c] = a;
+            pairs[8 * i + 4 + c] = b - a;
+        }
+    VR_CUDA(ctx, cudaMemcpy(ctx->d_tf, pairs.data(), pairs.size() * sizeof(float), cudaMemcpyHostToDevice));
     ctx->ntf = n;
     ctx->vmin = vmin;
     ctx->vmax = vmax;

@@ -25,7 +25,7 @@ struct BrickLaunch {
     float own_lo[3];    // ownership bounds in voxel units (-inf / +inf on volume faces)
     float own_hi[3];
     int sx, sy;         // haloed brick extents in x and y (elements)
-    long long base;     // element offset of the brick's haloed storage
+    long long base;     // quad offset of the brick's haloed xy-quad storage
     int rect[4];        // x0, y0, w, h of the footprint rectangle
     long long poff;     // float4 offset of the brick's partial
     int item_begin;     // first work item (tile) of this brick
@@ -46,9 +46,9 @@ struct MarchParams {
     float dt, inv_dt;   // sample spacing (world units) and its inverse
     float ert_T;        // terminate a brick when T <= ert_T (negative: never)
     // classification
-    float vmin, inv_range;
+    float tf_scale, tf_bias;  // x = s*scale + bias = (s - vmin)/(vmax - vmin)*(ntf-1)
     int ntf;
-    const float4 *tf;   // ntf entries
+    const float4 *tf;   // 2*ntf float4: (T[i], T[i+1]-T[i]) pairs, last difference 0
     const void *data;   // brick storage
     float4 *partials;   // partial pool
     unsigned long long *sample_counter;  // non-null: count executed samples
@@ -74,8 +74,7 @@ struct PackParams {
     void *dst;
     int N[3];
     int lo[3];
-    int s[3];       // haloed extents
-    long long count;
+    int s[3];       // haloed extents (the brick stores (s0-1)(s1-1)s2 quads)
 };
 
 // Launchers (vr_kernels.cu). They return the launch's cudaError_t.

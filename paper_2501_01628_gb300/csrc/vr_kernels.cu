@@ -14,50 +14,80 @@ namespace vr {
 namespace {
 
 // ---------------------------------------------------------------------------
-// Storage element loads (read-only path)
+// Brick storage: "xy-quads". Element (i,j,k) of a brick whose haloed extents
+// are (sx, sy, sz) holds the four voxels (i,j,k), (i+1,j,k), (i,j+1,k),
+// (i+1,j+1,k), for i < sx-1, j < sy-1, k < sz. A trilinear sample then needs
+// two vector loads (planes k and k+1) instead of eight scalar gathers, at four
+// times the storage -- L1 wavefronts, not HBM capacity, bound the march.
 // ---------------------------------------------------------------------------
-template <typename T> struct Elem;
-template <> struct Elem<float> {
-    static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
-};
-template <> struct Elem<__nv_bfloat16> {
-    static __device__ __forceinline__ float load(const __nv_bfloat16 *p)
+template <typename T> struct Quad;
+template <> struct Quad<float> {
+    using type = float4;
+    static __device__ __forceinline__ float4 load(const float4 *p) { return __ldg(p); }
+    static __device__ __forceinline__ float4 make(float a, float b, float c, float d)
     {
-        unsigned short u = __ldg(reinterpret_cast<const unsigned short *>(p));
-        return __uint_as_float(static_cast<unsigned>(u) << 16);
+        return make_float4(a, b, c, d);
     }
 };
-template <> struct Elem<__half> {
-    static __device__ __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
+template <> struct Quad<__nv_bfloat16> {
+    using type = uint2;
+    static __device__ __forceinline__ float4 load(const uint2 *p)
+    {
+        const uint2 u = __ldg(p);
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+    }
+    static __device__ __forceinline__ uint2 make(float a, float b, float c, float d)
+    {
+        auto bits = [](float v) {
+            return static_cast<unsigned>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
+        };
+        return make_uint2(bits(a) | (bits(b) << 16), bits(c) | (bits(d) << 16));
+    }
+};
+template <> struct Quad<__half> {
+    using type = uint2;
+    static __device__ __forceinline__ float4 load(const uint2 *p)
+    {
+        const uint2 u = __ldg(p);
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+    static __device__ __forceinline__ uint2 make(float a, float b, float c, float d)
+    {
+        auto bits = [](float v) { return static_cast<unsigned>(__half_as_ushort(__float2half_rn(v))); };
+        return make_uint2(bits(a) | (bits(b) << 16), bits(c) | (bits(d) << 16));
+    }
 };
 
 // ---------------------------------------------------------------------------
-// Pack: global x-fastest float32 volume -> one haloed brick in storage type
+// Pack: global x-fastest float32 volume -> one brick of xy-quads (halo of one
+// voxel, edge-clamped), converted to the storage type with round-to-nearest.
 // ---------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T to_storage(float v);
-template <> __device__ __forceinline__ float to_storage<float>(float v) { return v; }
-template <> __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(float v)
-{
-    return __float2bfloat16_rn(v);
-}
-template <> __device__ __forceinline__ __half to_storage<__half>(float v) { return __float2half_rn(v); }
-
 template <typename T>
 __global__ void pack_kernel(PackParams p)
 {
-    T *dst = static_cast<T *>(p.dst);
-    const long long sxy = static_cast<long long>(p.s[0]) * p.s[1];
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < p.count;
+    using Q = typename Quad<T>::type;
+    Q *dst = static_cast<Q *>(p.dst);
+    const int qx = p.s[0] - 1, qy = p.s[1] - 1;
+    const long long qxy = static_cast<long long>(qx) * qy;
+    const long long count = qxy * p.s[2];
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < count;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        int lz = static_cast<int>(e / sxy);
-        long long rem = e - lz * sxy;
-        int ly = static_cast<int>(rem / p.s[0]);
-        int lx = static_cast<int>(rem - static_cast<long long>(ly) * p.s[0]);
-        int gx = min(max(p.lo[0] + lx - 1, 0), p.N[0] - 1);
-        int gy = min(max(p.lo[1] + ly - 1, 0), p.N[1] - 1);
-        int gz = min(max(p.lo[2] + lz - 1, 0), p.N[2] - 1);
-        float v = p.src[(static_cast<long long>(gz) * p.N[1] + gy) * p.N[0] + gx];
-        dst[e] = to_storage<T>(v);
+        const int lz = static_cast<int>(e / qxy);
+        const long long rem = e - lz * qxy;
+        const int ly = static_cast<int>(rem / qx);
+        const int lx = static_cast<int>(rem - static_cast<long long>(ly) * qx);
+        const int gx0 = min(max(p.lo[0] + lx - 1, 0), p.N[0] - 1);
+        const int gx1 = min(max(p.lo[0] + lx, 0), p.N[0] - 1);
+        const int gy0 = min(max(p.lo[1] + ly - 1, 0), p.N[1] - 1);
+        const int gy1 = min(max(p.lo[1] + ly, 0), p.N[1] - 1);
+        const int gz = min(max(p.lo[2] + lz - 1, 0), p.N[2] - 1);
+        const float *plane = p.src + static_cast<long long>(gz) * p.N[1] * p.N[0];
+        const float *r0 = plane + static_cast<long long>(gy0) * p.N[0];
+        const float *r1 = plane + static_cast<long long>(gy1) * p.N[0];
+        dst[e] = Quad<T>::make(r0[gx0], r0[gx1], r1[gx0], r1[gx1]);
     }
 }
 
@@ -78,8 +108,9 @@ __device__ __forceinline__ int find_brick(const MarchParams &p, int item)
 template <typename S, bool COUNT>
 __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ MarchParams p)
 {
+    // transfer function as (T[i], T[i+1]-T[i]) pairs; the last difference is 0
     extern __shared__ float4 s_tf[];
-    for (int i = threadIdx.x; i < p.ntf; i += blockDim.x) s_tf[i] = p.tf[i];
+    for (int i = threadIdx.x; i < 2 * p.ntf; i += blockDim.x) s_tf[i] = p.tf[i];
     __syncthreads();
 
     const int item = blockIdx.x;
@@ -150,46 +181,53 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
         const float t_in = t0, t_out = t1;
         int k_first = max(0, static_cast<int>(floorf((b0 - t_in) * p.inv_dt - 0.5f)) - 1);
         int k_last = static_cast<int>(ceilf((fminf(b1, t_out) - t_in) * p.inv_dt - 0.5f)) + 1;
-        const S *vox = static_cast<const S *>(p.data) + B.base;
-        const int sx = B.sx, sxy = B.sx * B.sy;
+        using Q = typename Quad<S>::type;
+        const Q *vox = static_cast<const Q *>(p.data) + B.base;
+        const int qx = B.sx - 1, qxy = (B.sx - 1) * (B.sy - 1);
+        const float lx0 = static_cast<float>(B.lo[0] - 1), ly0 = static_cast<float>(B.lo[1] - 1),
+                    lz0 = static_cast<float>(B.lo[2] - 1);
+        const int imax = B.hi[0] - B.lo[0], jmax = B.hi[1] - B.lo[1], kmax = B.hi[2] - B.lo[2];
+        const float xmax = static_cast<float>(p.ntf - 1);
+        int prev = -1;
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
         bool entered = false;
         for (int k = k_first; k <= k_last; ++k) {
             const float t = fmaf(static_cast<float>(k) + 0.5f, p.dt, t_in);
             if (!(t < t_out)) break;
-            const float qx = fmaf(t, dv[0], ov[0]);
-            const float qy = fmaf(t, dv[1], ov[1]);
-            const float qz = fmaf(t, dv[2], ov[2]);
-            const bool own = qx >= B.own_lo[0] && qx < B.own_hi[0] && qy >= B.own_lo[1] &&
-                             qy < B.own_hi[1] && qz >= B.own_lo[2] && qz < B.own_hi[2];
+            const float qxv = fmaf(t, dv[0], ov[0]);
+            const float qyv = fmaf(t, dv[1], ov[1]);
+            const float qzv = fmaf(t, dv[2], ov[2]);
+            const bool own = qxv >= B.own_lo[0] && qxv < B.own_hi[0] && qyv >= B.own_lo[1] &&
+                             qyv < B.own_hi[1] && qzv >= B.own_lo[2] && qzv < B.own_hi[2];
             if (!own) {
                 if (entered) break;
                 continue;
             }
             entered = true;
-            // trilinear, clamp-to-edge through the halo
-            const float vx = qx - 0.5f, vy = qy - 0.5f, vz = qz - 0.5f;
+            // trilinear, clamp-to-edge through the halo; local voxel coordinates
+            const float vx = qxv - 0.5f - lx0, vy = qyv - 0.5f - ly0, vz = qzv - 0.5f - lz0;
             const float flx = floorf(vx), fly = floorf(vy), flz = floorf(vz);
             const float wx = vx - flx, wy = vy - fly, wz = vz - flz;
-            const int ix = min(max(static_cast<int>(flx), B.lo[0] - 1), B.hi[0] - 1) - B.lo[0] + 1;
-            const int iy = min(max(static_cast<int>(fly), B.lo[1] - 1), B.hi[1] - 1) - B.lo[1] + 1;
-            const int iz = min(max(static_cast<int>(flz), B.lo[2] - 1), B.hi[2] - 1) - B.lo[2] + 1;
-            const S *q = vox + (iz * sxy + iy * sx + ix);
-            const float v000 = Elem<S>::load(q), v100 = Elem<S>::load(q + 1);
-            const float v010 = Elem<S>::load(q + sx), v110 = Elem<S>::load(q + sx + 1);
-            const float v001 = Elem<S>::load(q + sxy), v101 = Elem<S>::load(q + sxy + 1);
-            const float v011 = Elem<S>::load(q + sxy + sx), v111 = Elem<S>::load(q + sxy + sx + 1);
-            const float c00 = fmaf(wx, v100 - v000, v000), c10 = fmaf(wx, v110 - v010, v010);
-            const float c01 = fmaf(wx, v101 - v001, v001), c11 = fmaf(wx, v111 - v011, v011);
+            const int ix = min(max(static_cast<int>(flx), 0), imax);
+            const int iy = min(max(static_cast<int>(fly), 0), jmax);
+            const int iz = min(max(static_cast<int>(flz), 0), kmax);
+            const int cell = iz * qxy + iy * qx + ix;
+            if (cell != prev) {  // consecutive samples often share a cell
+                q0 = Quad<S>::load(vox + cell);
+                q1 = Quad<S>::load(vox + cell + qxy);
+                prev = cell;
+            }
+            const float c00 = fmaf(wx, q0.y - q0.x, q0.x), c10 = fmaf(wx, q0.w - q0.z, q0.z);
+            const float c01 = fmaf(wx, q1.y - q1.x, q1.x), c11 = fmaf(wx, q1.w - q1.z, q1.z);
             const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
             const float s = fmaf(wz, c1 - c0, c0);
-            // classification
-            const float uu = fminf(fmaxf((s - p.vmin) * p.inv_range, 0.0f), 1.0f);
-            const float x = uu * static_cast<float>(p.ntf - 1);
-            const int ti = min(static_cast<int>(x), p.ntf - 2);
+            // classification: x = (s - vmin)/(vmax - vmin) * (n-1), clamped
+            const float x = fminf(fmaxf(fmaf(s, p.tf_scale, p.tf_bias), 0.0f), xmax);
+            const int ti = static_cast<int>(x);
             const float w = x - static_cast<float>(ti);
-            const float4 e0 = s_tf[ti], e1 = s_tf[ti + 1];
-            const float r = fmaf(w, e1.x - e0.x, e0.x), g = fmaf(w, e1.y - e0.y, e0.y);
-            const float bb = fmaf(w, e1.z - e0.z, e0.z), al = fmaf(w, e1.w - e0.w, e0.w);
+            const float4 e0 = s_tf[2 * ti], de = s_tf[2 * ti + 1];
+            const float r = fmaf(w, de.x, e0.x), g = fmaf(w, de.y, e0.y);
+            const float bb = fmaf(w, de.z, e0.z), al = fmaf(w, de.w, e0.w);
             // front-to-back emission-absorption
             const float ta = T * al;
             C0 = fmaf(ta, r, C0);
@@ -263,9 +301,10 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s)
 {
-    if (p.count <= 0) return cudaSuccess;
+    const long long count = static_cast<long long>(p.s[0] - 1) * (p.s[1] - 1) * p.s[2];
+    if (count <= 0) return cudaSuccess;
     const int threads = 256;
-    long long blocks = (p.count + threads - 1) / threads;
+    long long blocks = (count + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     switch (dtype) {
     case VR_F32: pack_kernel<float><<<static_cast<int>(blocks), threads, 0, s>>>(p); break;
@@ -280,7 +319,7 @@ cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s)
 {
     if (p.n_items <= 0) return cudaSuccess;
     const bool count = p.sample_counter != nullptr;
-    const size_t smem = static_cast<size_t>(p.ntf) * sizeof(float4);
+    const size_t smem = 2 * static_cast<size_t>(p.ntf) * sizeof(float4);
 #define VR_MARCH(T)                                                                      \
     (count ? (march_kernel<T, true><<<p.n_items, 128, smem, s>>>(p), 0)                  \
            : (march_kernel<T, false><<<p.n_items, 128, smem, s>>>(p), 0))

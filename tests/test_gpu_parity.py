@@ -46,7 +46,9 @@ def test_small_workload_full_image_partials_and_counts(vr):
         outside[y0:y0 + h, x0:x0 + w] = False
         assert np.all(ref["partials"][b][outside] == 0)
     assert got["nsamples"] == ref["nsamples"] == 256 * 256 * 128
-    assert list(got["order"][:4]) == [0, 1, 2, 3]  # z = low half first when looking along +z
+    # looking along +z: each brick of the low z half precedes the brick behind it
+    pos = {int(b): i for i, b in enumerate(got["order"])}
+    assert all(pos[b] < pos[b + 4] for b in range(4))
 
 
 # --------------------------------------------------------------------------
@@ -113,7 +115,11 @@ def test_early_termination(vr, grid):
     stats = compare_envelope(got["img"], env)
     assert stats["n_ambiguous"] < 0.02 * 96 * 54
     full = oracle.render(vol, boxes, tf, lo, hi, cam, 0.5, 1.0)
-    assert got["nsamples"] < full["nsamples"]  # termination saved work
+    # one brick holds whole chords, so termination saves work; small bricks may
+    # never reach T <= 0.01 locally
+    if grid == (1, 1, 1):
+        assert got["nsamples"] < full["nsamples"]
+    assert got["nsamples"] <= full["nsamples"]
     assert abs(got["nsamples"] - env["nsamples"]) <= 4 * max(1, stats["n_ambiguous"]) + 8
 
 
