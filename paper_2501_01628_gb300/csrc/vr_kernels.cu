@@ -109,9 +109,8 @@ template <typename S, bool COUNT>
 __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ MarchParams p)
 {
     // transfer function as (T[i], T[i+1]-T[i]) pairs; the last difference is 0
-    extern __shared__ float4 s_tf[];
-    for (int i = threadIdx.x; i < 2 * p.ntf; i += blockDim.x) s_tf[i] = p.tf[i];
-    __syncthreads();
+    // transfer-function pairs (8 KB for 256 entries) are read through L1: one
+    // cached copy per SM instead of one shared-memory copy per block
 
     const int item = blockIdx.x;
     const int bi = find_brick(p, item);
@@ -179,63 +178,100 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     unsigned long long executed = 0;
     if (hit && t0 < t1 && b0 <= b1) {
         const float t_in = t0, t_out = t1;
-        int k_first = max(0, static_cast<int>(floorf((b0 - t_in) * p.inv_dt - 0.5f)) - 1);
-        int k_last = static_cast<int>(ceilf((fminf(b1, t_out) - t_in) * p.inv_dt - 0.5f)) + 1;
-        using Q = typename Quad<S>::type;
-        const Q *vox = static_cast<const Q *>(p.data) + B.base;
-        const int qx = B.sx - 1, qxy = (B.sx - 1) * (B.sy - 1);
-        const float lx0 = static_cast<float>(B.lo[0] - 1), ly0 = static_cast<float>(B.lo[1] - 1),
-                    lz0 = static_cast<float>(B.lo[2] - 1);
-        const int imax = B.hi[0] - B.lo[0], jmax = B.hi[1] - B.lo[1], kmax = B.hi[2] - B.lo[2];
-        const float xmax = static_cast<float>(p.ntf - 1);
-        int prev = -1;
-        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
-        bool entered = false;
-        for (int k = k_first; k <= k_last; ++k) {
+        // Slab estimate of the samples this brick owns, widened by a margin that
+        // covers FP32 rounding of the positions (large only for rays nearly
+        // parallel to a face), then made exact with the ownership test itself.
+        float dmin = 3.0e38f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (dv[i] != 0.0f) dmin = fminf(dmin, fabsf(dv[i]));
+        const int margin = 2 + static_cast<int>(fminf(1.0e6f, 1.0e-6f * p.nmax / (dmin * p.dt)));
+        int ka = max(0, static_cast<int>(floorf((b0 - t_in) * p.inv_dt - 0.5f)) - margin);
+        int kb = static_cast<int>(ceilf((fminf(b1, t_out) - t_in) * p.inv_dt - 0.5f)) + margin;
+        // sample k is owned iff it lies before t_out and its cell is in the brick
+        // (same FP32 arithmetic for every brick: each sample has exactly one owner)
+        auto owned = [&](int k) {
             const float t = fmaf(static_cast<float>(k) + 0.5f, p.dt, t_in);
-            if (!(t < t_out)) break;
             const float qxv = fmaf(t, dv[0], ov[0]);
             const float qyv = fmaf(t, dv[1], ov[1]);
             const float qzv = fmaf(t, dv[2], ov[2]);
-            const bool own = qxv >= B.own_lo[0] && qxv < B.own_hi[0] && qyv >= B.own_lo[1] &&
-                             qyv < B.own_hi[1] && qzv >= B.own_lo[2] && qzv < B.own_hi[2];
-            if (!own) {
-                if (entered) break;
-                continue;
+            return t < t_out && qxv >= B.own_lo[0] && qxv < B.own_hi[0] && qyv >= B.own_lo[1] &&
+                   qyv < B.own_hi[1] && qzv >= B.own_lo[2] && qzv < B.own_hi[2];
+        };
+        while (ka <= kb && !owned(ka)) ++ka;
+        while (kb > ka && !owned(kb)) --kb;
+        // owned samples are contiguous along the ray: [ka, kb] are all owned
+        if (ka <= kb) {
+            using Q = typename Quad<S>::type;
+            const Q *vox = static_cast<const Q *>(p.data) + B.base;
+            const int qx = B.sx - 1, qxy = (B.sx - 1) * (B.sy - 1);
+            const int cell_max = qxy * (B.hi[2] - B.lo[2]) + qxy - 1;
+            const float xmax = static_cast<float>(p.ntf - 1);
+            // local voxel-centre coordinates v = q - lo + 1/2 as a linear function of k + 1/2
+            float base[3], step[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                step[i] = dv[i] * p.dt;
+                base[i] = fmaf(t_in, dv[i], ov[i] - (static_cast<float>(B.lo[i]) - 0.5f));
             }
-            entered = true;
-            // trilinear, clamp-to-edge through the halo; local voxel coordinates
-            const float vx = qxv - 0.5f - lx0, vy = qyv - 0.5f - ly0, vz = qzv - 0.5f - lz0;
-            const float flx = floorf(vx), fly = floorf(vy), flz = floorf(vz);
-            const float wx = vx - flx, wy = vy - fly, wz = vz - flz;
-            const int ix = min(max(static_cast<int>(flx), 0), imax);
-            const int iy = min(max(static_cast<int>(fly), 0), jmax);
-            const int iz = min(max(static_cast<int>(flz), 0), kmax);
-            const int cell = iz * qxy + iy * qx + ix;
-            if (cell != prev) {  // consecutive samples often share a cell
-                q0 = Quad<S>::load(vox + cell);
-                q1 = Quad<S>::load(vox + cell + qxy);
-                prev = cell;
+            // two samples per iteration: both cells' loads are issued before either
+            // sample is classified (independent memory requests in flight)
+            int prev = -1;
+            float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+            float kh = static_cast<float>(ka) + 0.5f;
+            auto locate = [&](float h, int &cell, float &wx, float &wy, float &wz) {
+                const float vx = fmaf(h, step[0], base[0]);
+                const float vy = fmaf(h, step[1], base[1]);
+                const float vz = fmaf(h, step[2], base[2]);
+                const float flx = floorf(vx), fly = floorf(vy), flz = floorf(vz);
+                wx = vx - flx;
+                wy = vy - fly;
+                wz = vz - flz;
+                cell = min(max(static_cast<int>(flz) * qxy + static_cast<int>(fly) * qx + static_cast<int>(flx), 0),
+                           cell_max);
+            };
+            auto shade = [&](const float4 &a0, const float4 &a1, float wx, float wy, float wz) {
+                const float c00 = fmaf(wx, a0.y - a0.x, a0.x), c10 = fmaf(wx, a0.w - a0.z, a0.z);
+                const float c01 = fmaf(wx, a1.y - a1.x, a1.x), c11 = fmaf(wx, a1.w - a1.z, a1.z);
+                const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
+                const float s = fmaf(wz, c1 - c0, c0);
+                const float x = fminf(fmaxf(fmaf(s, p.tf_scale, p.tf_bias), 0.0f), xmax);
+                const int ti = static_cast<int>(x);
+                const float w = x - static_cast<float>(ti);
+                const float4 e0 = __ldg(p.tf + 2 * ti), de = __ldg(p.tf + 2 * ti + 1);
+                const float r = fmaf(w, de.x, e0.x), g = fmaf(w, de.y, e0.y);
+                const float bb = fmaf(w, de.z, e0.z), al = fmaf(w, de.w, e0.w);
+                const float ta = T * al;
+                C0 = fmaf(ta, r, C0);
+                C1 = fmaf(ta, g, C1);
+                C2 = fmaf(ta, bb, C2);
+                T = T - ta;
+            };
+            for (int k = ka; k <= kb; k += 2, kh += 2.0f) {
+                int ca, cb;
+                float ax, ay, az, bx, by, bz;
+                locate(kh, ca, ax, ay, az);
+                const bool two = k < kb;
+                locate(kh + 1.0f, cb, bx, by, bz);
+                if (ca != prev) {
+                    q0 = Quad<S>::load(vox + ca);
+                    q1 = Quad<S>::load(vox + ca + qxy);
+                }
+                float4 r0 = q0, r1 = q1;
+                if (two && cb != ca) {
+                    r0 = Quad<S>::load(vox + cb);
+                    r1 = Quad<S>::load(vox + cb + qxy);
+                }
+                shade(q0, q1, ax, ay, az);
+                if (COUNT) ++executed;
+                if (T <= p.ert_T || !two) break;
+                shade(r0, r1, bx, by, bz);
+                if (COUNT) ++executed;
+                if (T <= p.ert_T) break;
+                q0 = r0;
+                q1 = r1;
+                prev = cb;
             }
-            const float c00 = fmaf(wx, q0.y - q0.x, q0.x), c10 = fmaf(wx, q0.w - q0.z, q0.z);
-            const float c01 = fmaf(wx, q1.y - q1.x, q1.x), c11 = fmaf(wx, q1.w - q1.z, q1.z);
-            const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
-            const float s = fmaf(wz, c1 - c0, c0);
-            // classification: x = (s - vmin)/(vmax - vmin) * (n-1), clamped
-            const float x = fminf(fmaxf(fmaf(s, p.tf_scale, p.tf_bias), 0.0f), xmax);
-            const int ti = static_cast<int>(x);
-            const float w = x - static_cast<float>(ti);
-            const float4 e0 = s_tf[2 * ti], de = s_tf[2 * ti + 1];
-            const float r = fmaf(w, de.x, e0.x), g = fmaf(w, de.y, e0.y);
-            const float bb = fmaf(w, de.z, e0.z), al = fmaf(w, de.w, e0.w);
-            // front-to-back emission-absorption
-            const float ta = T * al;
-            C0 = fmaf(ta, r, C0);
-            C1 = fmaf(ta, g, C1);
-            C2 = fmaf(ta, bb, C2);
-            T = T - ta;
-            if (COUNT) ++executed;
-            if (T <= p.ert_T) break;
         }
     }
     p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = make_float4(C0, C1, C2, 1.0f - T);
@@ -253,44 +289,95 @@ __device__ __forceinline__ float4 over(float4 front, float4 back)
                        fmaf(w, back.w, front.w));
 }
 
+// Per tile, warp 0 first compacts the bricks whose rectangles overlap the tile,
+// in visibility order. Absent partials are the identity of "over", so only the
+// association tree's carries at skipped positions matter; consecutive carries
+// compose to the deepest one, so each listed brick carries max(carry) up to the
+// next listed position.
 template <int LEVELS>
 __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ CompositeParams p)
 {
-    const int px = blockIdx.x * kCompW + threadIdx.x;
-    const int py = blockIdx.y * kCompH + threadIdx.y;
+    __shared__ int s_brick[kMaxBricks];
+    __shared__ int s_pos[kMaxBricks + 1];
+    __shared__ unsigned char s_carry[kMaxBricks];
+    __shared__ int s_m;
     const int tx0 = blockIdx.x * kCompW, ty0 = blockIdx.y * kCompH;
+    const int tid = threadIdx.y * kCompW + threadIdx.x;
+    if (tid < 32) {
+        int m = 0;
+        for (int j0 = 0; j0 < p.nb; j0 += 32) {
+            const int j = j0 + tid;
+            bool ov = false;
+            int b = 0;
+            if (j < p.nb) {
+                b = p.order[j];
+                const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
+                ov = x0 < tx0 + kCompW && tx0 < x0 + w && y0 < ty0 + kCompH && ty0 < y0 + h;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ov);
+            if (ov) {
+                const int at = m + __popc(bal & ((1u << tid) - 1u));
+                s_brick[at] = b;
+                s_pos[at] = j;
+            }
+            m += __popc(bal);
+        }
+        __syncwarp();
+        if (tid == 0) {
+            s_m = m;
+            s_pos[m] = p.nb;
+        }
+        __syncwarp();
+        if (LEVELS > 1)
+            for (int i = tid; i < m; i += 32) {
+                int c = 0;
+                for (int j = s_pos[i]; j < s_pos[i + 1]; ++j) c = max(c, static_cast<int>(p.carry[j]));
+                s_carry[i] = static_cast<unsigned char>(c);
+            }
+    }
+    __syncthreads();
+    const int m = s_m;
+    const int px = tx0 + threadIdx.x, py = ty0 + threadIdx.y;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 acc[LEVELS];
 #pragma unroll
-    for (int l = 0; l < LEVELS; ++l) acc[l] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int j = 0; j < p.nb; ++j) {
-        const int b = p.order[j];
-        const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
-        // block-uniform overlap test, then per-pixel containment
-        if (x0 < tx0 + kCompW && tx0 < x0 + w && y0 < ty0 + kCompH && ty0 < y0 + h) {
-            if (px >= x0 && px < x0 + w && py >= y0 && py < y0 + h && px < p.W && py < p.H) {
-                const float4 v = p.partials[p.poff[b] + static_cast<long long>(py - y0) * w + (px - x0)];
-                acc[0] = over(acc[0], v);
+    for (int l = 0; l < LEVELS; ++l) acc[l] = zero;
+    constexpr int kBatch = 4;  // partial loads in flight before they are combined
+    for (int i0 = 0; i0 < m; i0 += kBatch) {
+        float4 v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            v[u] = zero;
+            if (i0 + u < m) {
+                const int b = s_brick[i0 + u];
+                const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
+                if (px >= x0 && px < x0 + w && py >= y0 && py < y0 + h)
+                    v[u] = __ldcs(p.partials + p.poff[b] + static_cast<long long>(py - y0) * w + (px - x0));
             }
         }
-        if (LEVELS > 1) {
-            const int c = p.carry[j];
 #pragma unroll
-            for (int l = 0; l + 1 < LEVELS; ++l) {
-                if (l < c) {
-                    acc[l + 1] = over(acc[l + 1], acc[l]);
-                    acc[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < kBatch; ++u) {
+            if (i0 + u < m) {
+                acc[0] = over(acc[0], v[u]);
+                if (LEVELS > 1) {
+                    const int c = s_carry[i0 + u];
+#pragma unroll
+                    for (int l = 0; l + 1 < LEVELS; ++l) {
+                        if (l < c) {
+                            acc[l + 1] = over(acc[l + 1], acc[l]);
+                            acc[l] = zero;
+                        }
+                    }
                 }
             }
         }
     }
     if (px < p.W && py < p.H) {
         float4 r = acc[0];
-        if (LEVELS > 1) {
 #pragma unroll
-            for (int l = 1; l < LEVELS; ++l)
-                if (l == p.n_levels - 1) r = acc[l];
-        }
-        p.out[static_cast<long long>(py) * p.W + px] = r;
+        for (int l = 1; l < LEVELS; ++l)
+            if (l == p.n_levels - 1) r = acc[l];
+        __stcs(p.out + static_cast<long long>(py) * p.W + px, r);
     }
 }
 
@@ -319,10 +406,9 @@ cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s)
 {
     if (p.n_items <= 0) return cudaSuccess;
     const bool count = p.sample_counter != nullptr;
-    const size_t smem = 2 * static_cast<size_t>(p.ntf) * sizeof(float4);
 #define VR_MARCH(T)                                                                      \
-    (count ? (march_kernel<T, true><<<p.n_items, 128, smem, s>>>(p), 0)                  \
-           : (march_kernel<T, false><<<p.n_items, 128, smem, s>>>(p), 0))
+    (count ? (march_kernel<T, true><<<p.n_items, 128, 0, s>>>(p), 0)                     \
+           : (march_kernel<T, false><<<p.n_items, 128, 0, s>>>(p), 0))
     switch (dtype) {
     case VR_F32: VR_MARCH(float); break;
     case VR_BF16: VR_MARCH(__nv_bfloat16); break;
