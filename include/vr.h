@@ -200,6 +200,38 @@ vr_status vr_frame_release(vr_frame fr);
 vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on_device,
                           void *stream);
 
+/* ---- rendering without device allocation -------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that must
+ * not allocate device memory: a renderer embedded in a simulation that hands all
+ * device memory to its own pool allocator (in-situ use), or a caller on a
+ * latency-critical path where cudaMalloc/cudaFree, which synchronise the
+ * device, are not allowed.
+ *
+ * Renders one frame (steps 1 + 2 of vr_render_frame, direct composite) from
+ * caller-owned device memory: `volume_dev` is the x-fastest float32 volume of
+ * dims[0] x dims[1] x dims[2] voxels, read in place (no packed bricks); the
+ * image goes to `out_rgba_dev` (H x W x 4 float32, device). `tf_rgba` (n_tf
+ * RGBA entries, 2 <= n_tf <= 1024) and `cam` are host memory. Nothing is
+ * allocated on the device: the per-brick partial images and the transfer
+ * function live in one static device array of VR_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits. A frame whose
+ * partial images (16 bytes per pixel of every brick's footprint rectangle)
+ * would exceed it is rejected with VR_ERR_ARG before any device work.
+ *   - Works on the current CUDA device. The first call on each device looks up
+ *     the scratch address (cudaGetSymbolAddress); make that first call before
+ *     any stream capture.
+ *   - All calls on a device share the scratch: calls that overlap on the GPU
+ *     (other streams, other threads) race; order them on one stream. Each call
+ *     rewrites every scratch byte it reads, so nothing needs clearing.
+ *   - Asynchronous on `stream`; errors are returned as vr_status (no context,
+ *     so no vr_last_error text). */
+#define VR_NOALLOC_SCRATCH_BYTES (16u << 20)
+vr_status vr_render_frame_noalloc(const float *volume_dev, const int dims[3], const vr_partition *part,
+                                  const float *tf_rgba, int n_tf, float vmin, float vmax,
+                                  const vr_camera *cam, float step_voxels, float ert_alpha,
+                                  float *out_rgba_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

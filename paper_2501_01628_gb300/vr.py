@@ -34,7 +34,7 @@ EXPORTS = (
     "vr_set_composite_schedule", "vr_set_count_samples", "vr_get_sample_count",
     "vr_render_partials", "vr_frame_info", "vr_frame_partial", "vr_composite",
     "vr_frame_release", "vr_render_frame", "vr_partition_boxes", "vr_plan_view",
-    "vr_set_kernel_timing", "vr_get_kernel_timing",
+    "vr_set_kernel_timing", "vr_get_kernel_timing", "vr_render_frame_noalloc",
 )
 
 
@@ -83,6 +83,9 @@ _SIG = {
     "vr_set_kernel_timing": (_I, [_P, _I]),
     "vr_get_kernel_timing": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "vr_render_frame_noalloc": (_I, [_P, _P, ctypes.POINTER(vr_partition), _P, _I, ctypes.c_float,
+                                     ctypes.c_float, ctypes.POINTER(vr_camera), ctypes.c_float,
+                                     ctypes.c_float, _P, _P]),
     "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
     "vr_plan_view": (_I, [_P, ctypes.POINTER(vr_partition), ctypes.POINTER(vr_camera), _P, _P]),
 }
@@ -345,6 +348,26 @@ def vr_frame_release(frame):
 def vr_render_frame(ctx, vol, out, stream=None):
     ptr, on_dev, _ = _ptr_and_loc(out)
     _check(lib().vr_render_frame(ctx, vol, ptr, on_dev, _stream(stream)), ctx, "vr_render_frame")
+
+
+def vr_render_frame_noalloc(volume, partition, tf, vmin: float, vmax: float, cam: dict, out,
+                            step_voxels: float = 0.5, ert_alpha: float = 1.0, stream=None):
+    """Frame without device allocation: `volume` and `out` are caller-owned CUDA
+    tensors ([Nz, Ny, Nx] and [H, W, 4] float32); scratch is the library's static
+    device array (see include/vr.h)."""
+    vptr, von, vk = _ptr_and_loc(volume)
+    optr, oon, _ = _ptr_and_loc(out)
+    if not (von and oon):
+        raise ValueError("volume and out must be CUDA tensors")
+    nz, ny, nx = tuple(vk.shape)
+    dims = (ctypes.c_int * 3)(nx, ny, nz)
+    part, keep = make_partition(**(partition or {}))
+    t = np.ascontiguousarray(tf, dtype=np.float32).reshape(-1, 4)
+    c = camera_struct(cam)
+    _check(lib().vr_render_frame_noalloc(vptr, dims, ctypes.byref(part), t.ctypes.data, int(t.shape[0]),
+                                         float(vmin), float(vmax), ctypes.byref(c), float(step_voxels),
+                                         float(ert_alpha), optr, _stream(stream)), None,
+           "vr_render_frame_noalloc")
 
 
 # --------------------------------------------------------------------------
