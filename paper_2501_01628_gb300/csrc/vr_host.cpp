@@ -102,9 +102,13 @@ namespace {
 size_t elem_size(vr_dtype t) { return t == VR_F32 ? 4 : 2; }
 // bytes of one xy-quad (four voxels) in device storage
 size_t quad_size(vr_dtype t) { return 4 * elem_size(t); }
+// quads stored for a brick: haloed extents (sx, sy, sz) give (sx-1) x (sy-1) x sz
+// quads, rounded up to whole 2x2x2 blocks
 long long brick_quads(const int *bx)
 {
-    return static_cast<long long>(bx[3] - bx[0] + 1) * (bx[4] - bx[1] + 1) * (bx[5] - bx[2] + 2);
+    const long long nbx = (bx[3] - bx[0] + 2) / 2, nby = (bx[4] - bx[1] + 2) / 2,
+                    nbz = (bx[5] - bx[2] + 3) / 2;
+    return nbx * nby * nbz * 8;
 }
 
 vr_status fail(vr_ctx ctx, vr_status s, const std::string &msg)
@@ -469,6 +473,8 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
     mp.ortho = c.ortho ? 1 : 0;
     mp.W = c.width;
     mp.H = c.height;
+    mp.inv_W = static_cast<float>(1.0 / c.width);
+    mp.inv_H = static_cast<float>(1.0 / c.height);
     mp.nmax = static_cast<float>(nmax);
     const double dt = static_cast<double>(ctx->step) / nmax;
     mp.dt = static_cast<float>(dt);
@@ -834,14 +840,14 @@ vr_status vr_volume_read_brick(vr_volume vol, int brick, void *dst, size_t bytes
                                                vol->base[brick] * static_cast<long long>(4 * es),
                                  q.size(), cudaMemcpyDeviceToHost));
     // voxel (i,j,k) is component (i==sx-1) + 2*(j==sy-1) of quad (min(i,sx-2), min(j,sy-2), k)
-    const int qx = sx - 1, qy = sy - 1;
+    const int qx = sx - 1, qy = sy - 1, nbx = sx / 2, nby = sy / 2;
     unsigned char *out = static_cast<unsigned char *>(dst);
     for (int k = 0; k < sz; ++k)
         for (int j = 0; j < sy; ++j)
             for (int i = 0; i < sx; ++i) {
                 const int ii = std::min(i, qx - 1), jj = std::min(j, qy - 1);
                 const int c = (i == sx - 1 ? 1 : 0) + (j == sy - 1 ? 2 : 0);
-                const size_t src = ((static_cast<size_t>(k) * qy + jj) * qx + ii) * 4 + c;
+                const size_t src = static_cast<size_t>(quad_index(ii, jj, k, nbx, nby)) * 4 + c;
                 const size_t o = (static_cast<size_t>(k) * sy + j) * sx + i;
                 std::memcpy(out + o * es, q.data() + src * es, es);
             }

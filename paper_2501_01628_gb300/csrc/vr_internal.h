@@ -19,6 +19,15 @@ constexpr int kTileH = 8;
 constexpr int kCompW = 32;
 constexpr int kCompH = 8;
 
+// Brick storage index of quad (i, j, k): quads are grouped in 2x2x2 blocks of
+// 128 bytes (one L1 line for float32), blocks x-fastest; nbx, nby = blocks per
+// row and per plane. A warp's 8x4 ray packet then touches about the same
+// number of lines whatever the view direction.
+__host__ __device__ __forceinline__ int quad_index(int i, int j, int k, int nbx, int nby)
+{
+    return ((((k >> 1) * nby + (j >> 1)) * nbx + (i >> 1)) << 3) | ((k & 1) << 2) | ((j & 1) << 1) | (i & 1);
+}
+
 // Per-brick data of one frame, as the march kernel needs it.
 struct BrickLaunch {
     int lo[3], hi[3];   // voxel box, half-open
@@ -40,6 +49,7 @@ struct MarchParams {
     float ow, oh;       // orthographic image-plane extent
     int ortho;
     int W, H;
+    float inv_W, inv_H;  // 1/W, 1/H
     // volume
     float nmax;         // voxels per world unit
     float N[3];         // volume extent in voxels

@@ -70,7 +70,7 @@ __global__ void pack_kernel(PackParams p)
 {
     using Q = typename Quad<T>::type;
     Q *dst = static_cast<Q *>(p.dst);
-    const int qx = p.s[0] - 1, qy = p.s[1] - 1;
+    const int qx = p.s[0] - 1, qy = p.s[1] - 1, nbx = p.s[0] / 2, nby = p.s[1] / 2;
     const long long qxy = static_cast<long long>(qx) * qy;
     const long long count = qxy * p.s[2];
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < count;
@@ -87,7 +87,7 @@ __global__ void pack_kernel(PackParams p)
         const float *plane = p.src + static_cast<long long>(gz) * p.N[1] * p.N[0];
         const float *r0 = plane + static_cast<long long>(gy0) * p.N[0];
         const float *r1 = plane + static_cast<long long>(gy1) * p.N[0];
-        dst[e] = Quad<T>::make(r0[gx0], r0[gx1], r1[gx0], r1[gx1]);
+        dst[quad_index(lx, ly, lz, nbx, nby)] = Quad<T>::make(r0[gx0], r0[gx1], r1[gx0], r1[gx1]);
     }
 }
 
@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     const int px = B.rect[0] + rx, py = B.rect[1] + ry;
 
     // primary ray (FP32; identical arithmetic for every brick)
-    const float fx = (static_cast<float>(px) + 0.5f) / static_cast<float>(p.W);
-    const float fy = (static_cast<float>(py) + 0.5f) / static_cast<float>(p.H);
+    const float fx = (static_cast<float>(px) + 0.5f) * p.inv_W;
+    const float fy = (static_cast<float>(py) + 0.5f) * p.inv_H;
     float o[3], d[3];
     if (p.ortho) {
         const float a = (fx - 0.5f) * p.ow, b = (fy - 0.5f) * p.oh;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
             o[i] = p.eye[i];
             d[i] = fmaf(sy, p.u[i], fmaf(sx, p.r[i], p.f[i]));
         }
-        const float inv = 1.0f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const float inv = __frsqrt_rn(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
 #pragma unroll
         for (int i = 0; i < 3; ++i) d[i] *= inv;
     }
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
             if (ov[i] < 0.0f || ov[i] > p.N[i]) hit = false;
             if (ov[i] < static_cast<float>(B.lo[i]) || ov[i] > static_cast<float>(B.hi[i])) hit = false;
         } else {
-            const float inv = 1.0f / dv[i];
+            const float inv = __frcp_rn(dv[i]);
             float ta = (0.0f - ov[i]) * inv, tb = (p.N[i] - ov[i]) * inv;
             t0 = fmaxf(t0, fminf(ta, tb));
             t1 = fminf(t1, fmaxf(ta, tb));
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
 #pragma unroll
         for (int i = 0; i < 3; ++i)
             if (dv[i] != 0.0f) dmin = fminf(dmin, fabsf(dv[i]));
-        const int margin = 2 + static_cast<int>(fminf(1.0e6f, 1.0e-6f * p.nmax / (dmin * p.dt)));
+        const int margin = 2 + static_cast<int>(fminf(1.0e6f, __fdividef(1.0e-6f * p.nmax, dmin * p.dt)));
         int ka = max(0, static_cast<int>(floorf((b0 - t_in) * p.inv_dt - 0.5f)) - margin);
         int kb = static_cast<int>(ceilf((fminf(b1, t_out) - t_in) * p.inv_dt - 0.5f)) + margin;
         // sample k is owned iff it lies before t_out and its cell is in the brick
@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
         if (ka <= kb) {
             using Q = typename Quad<S>::type;
             const Q *vox = static_cast<const Q *>(p.data) + B.base;
-            const int qx = B.sx - 1, qxy = (B.sx - 1) * (B.sy - 1);
-            const int cell_max = qxy * (B.hi[2] - B.lo[2]) + qxy - 1;
+            const int nbx = B.sx / 2, nby = B.sy / 2;
+            const int imax = B.hi[0] - B.lo[0], jmax = B.hi[1] - B.lo[1], kmax = B.hi[2] - B.lo[2];
             const float xmax = static_cast<float>(p.ntf - 1);
             // local voxel-centre coordinates v = q - lo + 1/2 as a linear function of k + 1/2
             float base[3], step[3];
@@ -219,7 +219,9 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
             int prev = -1;
             float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
             float kh = static_cast<float>(ka) + 0.5f;
-            auto locate = [&](float h, int &cell, float &wx, float &wy, float &wz) {
+            // quad indices of planes k and k+1 of the sample's cell; the clamps
+            // only guard memory (owned samples always lie inside the brick)
+            auto locate = [&](float h, int &cell, int &cell1, float &wx, float &wy, float &wz) {
                 const float vx = fmaf(h, step[0], base[0]);
                 const float vy = fmaf(h, step[1], base[1]);
                 const float vz = fmaf(h, step[2], base[2]);
@@ -227,8 +229,11 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
                 wx = vx - flx;
                 wy = vy - fly;
                 wz = vz - flz;
-                cell = min(max(static_cast<int>(flz) * qxy + static_cast<int>(fly) * qx + static_cast<int>(flx), 0),
-                           cell_max);
+                const int i = min(max(static_cast<int>(flx), 0), imax);
+                const int j = min(max(static_cast<int>(fly), 0), jmax);
+                const int k = min(max(static_cast<int>(flz), 0), kmax);
+                cell = quad_index(i, j, k, nbx, nby);
+                cell1 = quad_index(i, j, k + 1, nbx, nby);
             };
             auto shade = [&](const float4 &a0, const float4 &a1, float wx, float wy, float wz) {
                 const float c00 = fmaf(wx, a0.y - a0.x, a0.x), c10 = fmaf(wx, a0.w - a0.z, a0.z);
@@ -248,19 +253,19 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
                 T = T - ta;
             };
             for (int k = ka; k <= kb; k += 2, kh += 2.0f) {
-                int ca, cb;
+                int ca, ca1, cb, cb1;
                 float ax, ay, az, bx, by, bz;
-                locate(kh, ca, ax, ay, az);
+                locate(kh, ca, ca1, ax, ay, az);
                 const bool two = k < kb;
-                locate(kh + 1.0f, cb, bx, by, bz);
+                locate(kh + 1.0f, cb, cb1, bx, by, bz);
                 if (ca != prev) {
                     q0 = Quad<S>::load(vox + ca);
-                    q1 = Quad<S>::load(vox + ca + qxy);
+                    q1 = Quad<S>::load(vox + ca1);
                 }
                 float4 r0 = q0, r1 = q1;
                 if (two && cb != ca) {
                     r0 = Quad<S>::load(vox + cb);
-                    r1 = Quad<S>::load(vox + cb + qxy);
+                    r1 = Quad<S>::load(vox + cb1);
                 }
                 shade(q0, q1, ax, ay, az);
                 if (COUNT) ++executed;

@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(128) march_global_kernel(const __grid_constant
     if (rx >= B.rect[2] || ry >= B.rect[3]) return;
     const int px = B.rect[0] + rx, py = B.rect[1] + ry;
 
-    const float fx = (static_cast<float>(px) + 0.5f) / static_cast<float>(p.W);
-    const float fy = (static_cast<float>(py) + 0.5f) / static_cast<float>(p.H);
+    const float fx = (static_cast<float>(px) + 0.5f) * p.inv_W;
+    const float fy = (static_cast<float>(py) + 0.5f) * p.inv_H;
     float o[3], d[3];
     if (p.ortho) {
         const float a = (fx - 0.5f) * p.ow, b = (fy - 0.5f) * p.oh;
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(128) march_global_kernel(const __grid_constant
             o[i] = p.eye[i];
             d[i] = fmaf(sy, p.u[i], fmaf(sx, p.r[i], p.f[i]));
         }
-        const float inv = 1.0f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const float inv = __frsqrt_rn(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         for (int i = 0; i < 3; ++i) d[i] *= inv;
     }
     float ov[3], dv[3];
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(128) march_global_kernel(const __grid_constant
             if (ov[i] < 0.0f || ov[i] > p.N[i]) hit = false;
             if (ov[i] < static_cast<float>(B.lo[i]) || ov[i] > static_cast<float>(B.hi[i])) hit = false;
         } else {
-            const float inv = 1.0f / dv[i];
+            const float inv = __frcp_rn(dv[i]);
             float ta = (0.0f - ov[i]) * inv, tb = (p.N[i] - ov[i]) * inv;
             t0 = fmaxf(t0, fminf(ta, tb));
             t1 = fminf(t1, fmaxf(ta, tb));
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(128) march_global_kernel(const __grid_constant
         float dmin = 3.0e38f;
         for (int i = 0; i < 3; ++i)
             if (dv[i] != 0.0f) dmin = fminf(dmin, fabsf(dv[i]));
-        const int margin = 2 + static_cast<int>(fminf(1.0e6f, 1.0e-6f * p.nmax / (dmin * p.dt)));
+        const int margin = 2 + static_cast<int>(fminf(1.0e6f, __fdividef(1.0e-6f * p.nmax, dmin * p.dt)));
         int ka = max(0, static_cast<int>(floorf((b0 - t_in) * p.inv_dt - 0.5f)) - margin);
         int kb = static_cast<int>(ceilf((fminf(b1, t_out) - t_in) * p.inv_dt - 0.5f)) + margin;
         auto owned = [&](int k) {
@@ -261,6 +261,8 @@ extern "C" vr_status vr_render_frame_noalloc(const float *volume_dev, const int 
     mp.ortho = cam->ortho ? 1 : 0;
     mp.W = cam->width;
     mp.H = cam->height;
+    mp.inv_W = static_cast<float>(1.0 / cam->width);
+    mp.inv_H = static_cast<float>(1.0 / cam->height);
     mp.nmax = static_cast<float>(nmax);
     const double dt = static_cast<double>(step_voxels) / nmax;
     mp.dt = static_cast<float>(dt);
