@@ -51,6 +51,27 @@ def args_parse():
     return ap.parse_args()
 
 
+def recorded_traffic():
+    """DRAM bytes per march launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "march_paper_workload.md")
+    csrc = os.path.join(ROOT, "paper_2501_01628_gb300", "csrc")
+    try:
+        text = open(path).read()
+        h = hashlib.sha256()
+        for f in ("vr_kernels.cu", "vr_internal.h"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    k = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not k or k.group(1) != h.hexdigest()[:16]:
+        return None
+    return float(m.group(1))
+
+
 def workload(name: str):
     import numpy as np
     from paper_2501_01628_gb300 import synth
@@ -335,9 +356,12 @@ def run_ours(a):
         gpu_launches=2 * K,
         clocks=clk,
         roofline=dict(bound="alu", kernel="march", achieved=march_tflops, peak=fp32_peak, unit="TFLOP/s",
-                      frac=march_tflops / fp32_peak, traffic=None,
+                      frac=march_tflops / fp32_peak,
+                      traffic=recorded_traffic() if a.workload == "paper" else None,
                       note="FP32 %d flops/sample x executed samples / mean march launch; peak = 152 SMs x "
                            "128 lanes x 2 x %.0f MHz (derived)" % (FLOPS_PER_SAMPLE, sm_max)),
+        roofline_l1=dict(note="ncu: L1 data-pipe LSU wavefronts 90% of peak on the march "
+                              "(profiles/march_paper_workload.md): the unit that binds it"),
         roofline_hbm=dict(march=dict(achieved=march_hbm_gbs, peak=hbm, unit="GB/s", frac=march_hbm_gbs / hbm,
                                      note="compulsory bytes (volume once + partial writes) / march time, %s"
                                           % hbm_src),
