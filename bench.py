@@ -46,7 +46,7 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small", "precision"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -376,8 +376,85 @@ def run_ours(a):
     print(json.dumps(line))
 
 
+def run_precision(a):
+    """Precision form: the 1024^3 blob volume (seed 2, 64 kd bricks, 2048^2
+    perspective) stored as float32, bfloat16 and float16; frame time of each and,
+    for the 16-bit forms, the error against the FP64 oracle on the centre 256^2
+    crop (accumulation error: oracle on the same quantised values; total error:
+    oracle on the float32 source)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    import oracle
+    from paper_2501_01628_gb300 import synth, vr
+    __graft_entry__.build()
+    n = 1024
+    vol, tf, cuts = synth.precision_scene(n=n)
+    lo, hi = synth.volume_range(vol)
+    part = dict(kind="kd", n_bricks=64, cut_fracs=cuts)
+    boxes = oracle.kd_partition((n,) * 3, 64, cuts)
+    cam = synth.orbit_camera(2048, 2048, 30.0)
+    crop = (896, 896, 256, 256)
+    tfs = dict(workload=tf, ramp=synth.ramp_tf())
+    ref_total = {k: oracle.render(vol, boxes, t, lo, hi, cam, 0.5, crop=crop)["img"] for k, t in tfs.items()}
+    quantised = {s: synth.quantize(vol, s) for s in ("bf16", "f16")}
+    vol_dev = torch.from_numpy(vol).cuda()
+    out = torch.empty((2048, 2048, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    forms = {}
+    for storage in ("f32", "bf16", "f16"):
+        ctx = vr.vr_create(0)
+        v = vr.vr_volume_create(ctx, vol_dev, storage, part)
+        vr.vr_set_transfer_function(ctx, tf, lo, hi)
+        vr.vr_set_render_params(ctx, 0.5, 1.0)
+        vr.vr_set_camera(ctx, cam)
+        vr.vr_set_count_samples(ctx, True)
+        vr.vr_render_frame(ctx, v, out)
+        nsamp = vr.vr_get_sample_count(ctx)
+        vr.vr_set_count_samples(ctx, False)
+        for _ in range(a.warmup):
+            vr.vr_render_frame(ctx, v, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            vr.vr_render_frame(ctx, v, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        _, nbytes = vr.vr_volume_info(v)
+        f = dict(ms_per_frame=ms, samples_per_s=nsamp / (ms / 1e3), storage_bytes=nbytes)
+        for kind, t in tfs.items():
+            vr.vr_set_transfer_function(ctx, t, lo, hi)
+            vr.vr_render_frame(ctx, v, out)
+            img = out[896:1152, 896:1152].cpu().numpy().astype(np.float64)
+            e = dict(err_total_mean=float(np.mean(np.abs(img - ref_total[kind]))),
+                     err_total_max=float(np.max(np.abs(img - ref_total[kind]))))
+            if storage != "f32":
+                code = oracle.BF16 if storage == "bf16" else oracle.F16
+                ref_q = oracle.render(quantised[storage], boxes, t, lo, hi, cam, 0.5, crop=crop,
+                                      dtype=code)["img"]
+                e["err_accumulation_max"] = float(np.max(np.abs(img - ref_q)))
+            f["tf_" + kind] = e
+        forms[storage] = f
+        vr.vr_volume_release(v)
+        vr.vr_destroy(ctx)
+    for s in ("bf16", "f16"):
+        forms[s]["speedup_vs_f32"] = forms["f32"]["ms_per_frame"] / forms[s]["ms_per_frame"]
+    line = dict(metric=METRIC, value=forms["bf16"]["samples_per_s"], unit=UNIT, n_gpus=1, steps=a.steps,
+                warmup=a.warmup, ms_per_step=forms["bf16"]["ms_per_frame"], higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="bf16 storage, f32 arithmetic", data="synthetic",
+                config=dict(workload="precision: 1024^3 blobs (seed 2), 64 kd bricks, 2048x2048 perspective "
+                                     "(azimuth 30 deg), step 0.5 voxel; error on the centre 256^2 crop"),
+                forms=forms, gpu_launches=2 * a.steps)
+    print(json.dumps(line))
+
+
 def main():
     a = args_parse()
+    if a.workload == "precision":
+        run_precision(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

@@ -126,6 +126,14 @@ def random_tf(rng: np.random.Generator, n_entries: int = 256, n_points: int = 4,
     return table.astype(np.float32)
 
 
+def ramp_tf(n_entries: int = 256, alpha_max: float = 0.05) -> np.ndarray:
+    """Deterministic table whose opacity and colour change across the whole
+    range (alpha = alpha_max*u, rgb = (u, 1-u, 1/2)): every change of the scalar
+    shows in the image, which makes storage-precision effects visible."""
+    u = np.arange(n_entries, dtype=np.float64) / (n_entries - 1)
+    return np.stack([u, 1.0 - u, np.full_like(u, 0.5), alpha_max * u], axis=1).astype(np.float32)
+
+
 def constant_tf(rgba, n_entries: int = 256) -> np.ndarray:
     return np.tile(np.asarray(rgba, dtype=np.float32)[None, :], (n_entries, 1))
 
@@ -196,6 +204,26 @@ def noise_blob_scene(n: int = 512, seed: int = 1, n_blobs: int = 16):
     blob_volume(n, blobs, out=vol)
     tf = random_tf(rng)
     return vol, tf
+
+
+def precision_scene(n: int = 1024, seed: int = 2, n_bricks: int = 64, n_blobs: int = 8):
+    """Blob volume of the small workload's generator at n^3 plus its TF, then
+    n_bricks-1 kd cut fractions U[0.3, 0.7] (seed order: blobs, TF, cuts)."""
+    rng = np.random.default_rng(seed)
+    blobs = draw_blobs(rng, n_blobs)
+    vol = blob_volume(n, blobs)
+    tf = random_tf(rng)
+    cuts = kd_cut_fractions(rng, n_bricks)
+    return vol, tf, cuts
+
+
+def quantize(vol: np.ndarray, storage: str) -> np.ndarray:
+    """Round-to-nearest-even bf16/f16 bits (uint16) of a float32 volume, as
+    torch's CPU conversion produces them."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(vol, dtype=np.float32))
+    t = t.to(torch.bfloat16 if storage == "bf16" else torch.float16)
+    return t.view(torch.int16).numpy().view(np.uint16)
 
 
 def volume_range(vol: np.ndarray):
