@@ -60,7 +60,8 @@ class _Scene(ctypes.Structure):
                 ("ntf", ctypes.c_int), ("vmin", ctypes.c_double),
                 ("vmax", ctypes.c_double), ("cam", _Camera),
                 ("step_voxels", ctypes.c_double), ("ert_alpha", ctypes.c_double),
-                ("ert_bias", ctypes.c_double), ("end_bias", ctypes.c_double)]
+                ("ert_bias", ctypes.c_double), ("end_bias", ctypes.c_double),
+                ("tf64", ctypes.c_void_p)]
 
 
 def lib():
@@ -76,6 +77,10 @@ def lib():
             _lib.orc_grid_partition.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             _lib.orc_kd_partition.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p]
+            _lib.orc_render_grad.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int]
+            _lib.orc_render_grad.restype = ctypes.c_int
             _lib.orc_sample.argtypes = [ctypes.POINTER(_Scene), ctypes.c_void_p]
             _lib.orc_sample.restype = ctypes.c_double
             _lib.orc_classify.argtypes = [ctypes.POINTER(_Scene), ctypes.c_double, ctypes.c_void_p]
@@ -136,8 +141,12 @@ def _scene(vol, boxes, tf, vmin, vmax, cam, step_voxels, ert_alpha, dtype, keep)
     vol = np.ascontiguousarray(vol)
     code = _dtype_code(vol, dtype)
     boxes = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 6)
-    tf = np.ascontiguousarray(tf, dtype=np.float32).reshape(-1, 4)
-    keep.extend([vol, boxes, tf])
+    tf_in = np.asarray(tf)
+    tf64 = None
+    if tf_in.dtype == np.float64:  # exact table (finite-difference probes)
+        tf64 = np.ascontiguousarray(tf_in).reshape(-1, 4)
+    tf = np.ascontiguousarray(tf_in, dtype=np.float32).reshape(-1, 4)
+    keep.extend([vol, boxes, tf, tf64])
     sc = _Scene()
     sc.vol = vol.ctypes.data
     sc.dtype = code
@@ -150,6 +159,7 @@ def _scene(vol, boxes, tf, vmin, vmax, cam, step_voxels, ert_alpha, dtype, keep)
     sc.cam = _camera(cam)
     sc.step_voxels = float(step_voxels)
     sc.ert_alpha = float(ert_alpha)
+    sc.tf64 = tf64.ctypes.data if tf64 is not None else None
     return sc
 
 
@@ -225,6 +235,33 @@ def render(vol: np.ndarray, boxes, tf: np.ndarray, vmin: float, vmax: float, cam
         if parts is not None:
             parts = parts.reshape((sc.nb,) + shape + (4,))
     return dict(img=img, partials=parts, nsamples=int(ns.value))
+
+
+def render_grad(vol, boxes, tf, vmin, vmax, cam, grad_img, step_voxels: float = 0.5, pixels=None,
+                crop=None, dtype=None, want_volume: bool = True, threads: int | None = None):
+    """Vector-Jacobian product of the rendered pixels: returns (dL/dT (ntf, 4),
+    dL/dv (vol.shape) or None) for the upstream gradient grad_img (same shape as
+    the rendered pixels, RGBA). Early termination is off."""
+    keep = []
+    sc = _scene(vol, boxes, tf, vmin, vmax, cam, step_voxels, 1.0, dtype, keep)
+    W, H = int(cam["width"]), int(cam["height"])
+    if pixels is None:
+        x0, y0, w, h = crop if crop is not None else (0, 0, W, H)
+        ys, xs = np.mgrid[y0:y0 + h, x0:x0 + w]
+        pixels = np.stack([xs.ravel(), ys.ravel()], axis=1)
+    pix = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
+    g = np.ascontiguousarray(grad_img, dtype=np.float64).reshape(-1, 4)
+    if g.shape[0] != pix.shape[0]:
+        raise ValueError("grad_img must hold one RGBA row per pixel")
+    gtf = np.zeros((sc.ntf, 4), np.float64)
+    gvol = np.zeros(np.asarray(vol).shape, np.float64) if want_volume else None
+    nthreads = threads if threads is not None else (os.cpu_count() or 1)
+    rc = lib().orc_render_grad(ctypes.byref(sc), pix.shape[0], pix.ctypes.data, g.ctypes.data,
+                               gtf.ctypes.data, gvol.ctypes.data if gvol is not None else None,
+                               int(nthreads))
+    if rc != 0:
+        raise RuntimeError("oracle gradient failed (%d)" % rc)
+    return gtf, gvol
 
 
 # Decision-ambiguity probes. A float decides two integers per ray: how many

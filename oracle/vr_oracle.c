@@ -55,6 +55,7 @@ typedef struct {
     double ert_alpha;       /* early termination opacity; >= 1 disables */
     double ert_bias;        /* added to the termination threshold (ambiguity probes) */
     double end_bias;        /* added to t_out in the sample-count test (ambiguity probes) */
+    const double *tf64;     /* optional: ntf x 4 table in double, used instead of tf */
 } orc_scene;
 
 /* ---- scalar helpers ---------------------------------------------------- */
@@ -135,6 +136,11 @@ static double sample_trilinear(const orc_scene *sc, const double p[3])
  * global range; entry i of n sits at u = i/(n-1); x = u(n-1),
  * i = min(floor(x), n-2), w = x - i, rgba = (1-w) T[i] + w T[i+1]. The alpha is
  * the opacity of one sample at the configured step (no step correction). */
+static double tf_entry(const orc_scene *sc, int i, int c)
+{
+    return sc->tf64 ? sc->tf64[4 * i + c] : (double)sc->tf[4 * i + c];
+}
+
 static void classify(const orc_scene *sc, double s, double rgba[4])
 {
     double u = clampd((s - sc->vmin) / (sc->vmax - sc->vmin), 0.0, 1.0);
@@ -143,7 +149,7 @@ static void classify(const orc_scene *sc, double s, double rgba[4])
     if (i > sc->ntf - 2) i = sc->ntf - 2;
     double w = x - i;
     for (int c = 0; c < 4; ++c)
-        rgba[c] = (1.0 - w) * (double)sc->tf[4 * i + c] + w * (double)sc->tf[4 * (i + 1) + c];
+        rgba[c] = (1.0 - w) * tf_entry(sc, i, c) + w * tf_entry(sc, i + 1, c);
 }
 
 /* ---- primary rays (Sec. 2.1: rays originate at the virtual camera) -----
@@ -414,6 +420,185 @@ int orc_kd_partition(const int dims[3], int n, const double *u, int *boxes)
         nbx[axis] = cut;
     }
     return 0;
+}
+
+/* ---- gradients (vector-Jacobian product of the rendered pixels) ---------
+ * For pixels (m x 2) and an upstream gradient G (m x 4, dL/dI per channel),
+ * adds dL/dT (the ntf x 4 table) to grad_tf and dL/dv (every voxel, x fastest)
+ * to grad_vol (may be NULL). Early termination must be off. The derivation is
+ * the chain rule through the readings above, written out step by step:
+ *   composite: I = C_front + F_b (C_b + (1 - A_b) R_b), with F_b the
+ *     transmittance in front of brick b and (R_b, 1 - Tb_b) the composite of the
+ *     bricks behind it, so dI_rgb/dC_b = F_b, dI_rgb/dA_b = -F_b R_b,
+ *     dI_A/dA_b = F_b Tb_b;
+ *   per brick: C_{k+1} = C_k + T_k a_k c_k, T_{k+1} = T_k (1 - a_k), A = 1 - T_n,
+ *     so with lambda_T(n) = -dL/dA and lambda_C = dL/dC:
+ *     dL/dc_k = lambda_C T_k a_k, dL/da_k = T_k (lambda_C . c_k) - T_k lambda_T(k+1),
+ *     lambda_T(k) = lambda_T(k+1) (1 - a_k) + a_k (lambda_C . c_k);
+ *   table: rgba = (1-w) T[i] + w T[i+1] gives dT[i] += (1-w) g, dT[i+1] += w g,
+ *     and ds = (g . (T[i+1] - T[i])) (n-1)/(vmax - vmin) where u is not clamped;
+ *   trilinear: dv(corner) += ds * weight(corner), on the clamped global indices.
+ * This oracle stores every sample of a ray (it is not the checkpointed GPU
+ * adjoint); there is no division by a transmittance anywhere. */
+typedef struct {
+    double p[3], s, x, rgba[4];
+    int brick;
+} orc_sample_rec;
+
+static void add_grad_tf(const orc_scene *sc, double *grad_tf, double x, const double g[4])
+{
+    int i = (int)floor(x);
+    if (i > sc->ntf - 2) i = sc->ntf - 2;
+    double w = x - i;
+    for (int c = 0; c < 4; ++c) {
+#pragma omp atomic
+        grad_tf[4 * i + c] += (1.0 - w) * g[c];
+#pragma omp atomic
+        grad_tf[4 * (i + 1) + c] += w * g[c];
+    }
+}
+
+static void add_grad_vol(const orc_scene *sc, double *grad_vol, const double p[3], double ds)
+{
+    const int nm = nmax3(sc->dims);
+    int i0[3], i1[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double v = p[a] * nm - 0.5;
+        double fl = floor(v);
+        f[a] = v - fl;
+        i0[a] = clampi((long long)fl, 0, sc->dims[a] - 1);
+        i1[a] = clampi((long long)fl + 1, 0, sc->dims[a] - 1);
+    }
+    const long long nx = sc->dims[0], nxy = (long long)sc->dims[0] * sc->dims[1];
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                long long idx = (dz ? i1[2] : i0[2]) * nxy + (dy ? i1[1] : i0[1]) * nx + (dx ? i1[0] : i0[0]);
+#pragma omp atomic
+                grad_vol[idx] += ds * w;
+            }
+}
+
+int orc_render_grad(const orc_scene *sc, int m, const int *pix, const double *grad_img, double *grad_tf,
+                    double *grad_vol, int nthreads)
+{
+    if (!sc || sc->nb < 1 || sc->ntf < 2 || !(sc->vmax > sc->vmin) || sc->step_voxels <= 0 ||
+        sc->ert_alpha < 1.0)
+        return -2;
+    const int nm = nmax3(sc->dims);
+    const double E[3] = {(double)sc->dims[0] / nm, (double)sc->dims[1] / nm, (double)sc->dims[2] / nm};
+    const double dt = sc->step_voxels / nm;
+    const double dxds = (sc->ntf - 1) / (sc->vmax - sc->vmin);
+    int fail = 0;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel num_threads(nthreads) reduction(| : fail)
+    {
+        long long cap = 1024;
+        orc_sample_rec *rec = (orc_sample_rec *)malloc(sizeof(orc_sample_rec) * cap);
+        int *first = (int *)malloc(sizeof(int) * (sc->nb + 1)); /* run start per visited brick */
+        int *bid = (int *)malloc(sizeof(int) * (sc->nb + 1));
+        double *Cb = (double *)malloc(sizeof(double) * 3 * sc->nb), *Ab = (double *)malloc(sizeof(double) * sc->nb);
+        double *Tk = NULL;
+        long long tk_cap = 0;
+        if (!rec || !first || !bid || !Cb || !Ab) fail = 1;
+#pragma omp for schedule(dynamic, 8)
+        for (int q = 0; q < m; ++q) {
+            if (fail) continue;
+            double o[3], d[3], t_in, t_out;
+            primary_ray(&sc->cam, pix[2 * q], pix[2 * q + 1], o, d);
+            if (!volume_interval(E, o, d, &t_in, &t_out)) continue;
+            /* samples in ray order with their owners; owners form contiguous runs */
+            long long n = 0;
+            int runs = 0, cur = 0;
+            for (long long k = 0;; ++k) {
+                double t = t_in + (k + 0.5) * dt;
+                if (!(t < t_out)) break;
+                if (n == cap) {
+                    cap *= 2;
+                    orc_sample_rec *r2 = (orc_sample_rec *)realloc(rec, sizeof(orc_sample_rec) * cap);
+                    if (!r2) { fail = 1; break; }
+                    rec = r2;
+                }
+                orc_sample_rec *r = rec + n;
+                int c[3];
+                for (int a = 0; a < 3; ++a) {
+                    r->p[a] = o[a] + t * d[a];
+                    c[a] = clampi((long long)floor(r->p[a] * nm), 0, sc->dims[a] - 1);
+                }
+                if (!in_box(sc->boxes + 6 * cur, c)) {
+                    cur = -1;
+                    for (int b = 0; b < sc->nb; ++b)
+                        if (in_box(sc->boxes + 6 * b, c)) { cur = b; break; }
+                    if (cur < 0) { fail = 2; break; }
+                }
+                if (runs == 0 || bid[runs - 1] != cur) {
+                    if (runs == sc->nb) { fail = 2; break; } /* a brick met twice: boxes not convex */
+                    bid[runs] = cur;
+                    first[runs] = (int)n;
+                    ++runs;
+                }
+                r->brick = cur;
+                r->s = sample_trilinear(sc, r->p);
+                r->x = clampd((r->s - sc->vmin) / (sc->vmax - sc->vmin), 0.0, 1.0) * (sc->ntf - 1);
+                classify(sc, r->s, r->rgba);
+                ++n;
+            }
+            if (fail) continue;
+            first[runs] = (int)n;
+            if (n > tk_cap) {
+                free(Tk);
+                tk_cap = n + 1;
+                Tk = (double *)malloc(sizeof(double) * tk_cap);
+                if (!Tk) { fail = 1; continue; }
+            }
+            /* forward per run: T_k and the partial (C, A) */
+            for (int j = 0; j < runs; ++j) {
+                double C[3] = {0, 0, 0}, T = 1.0;
+                for (int k = first[j]; k < first[j + 1]; ++k) {
+                    Tk[k] = T;
+                    const double *g = rec[k].rgba;
+                    for (int ch = 0; ch < 3; ++ch) C[ch] += T * g[3] * g[ch];
+                    T *= 1.0 - g[3];
+                }
+                for (int ch = 0; ch < 3; ++ch) Cb[3 * j + ch] = C[ch];
+                Ab[j] = 1.0 - T;
+            }
+            /* composite adjoint: front transmittance F (forward sweep), behind
+             * composite (R, Tb) (backward sweep) */
+            const double *G = grad_img + 4 * (long long)q;
+            double R[3] = {0, 0, 0}, Tb = 1.0;
+            for (int j = runs - 1; j >= 0; --j) {
+                double F = 1.0;
+                for (int a = 0; a < j; ++a) F *= 1.0 - Ab[a];
+                double gC[3] = {F * G[0], F * G[1], F * G[2]};
+                double gA = F * (G[3] * Tb - (G[0] * R[0] + G[1] * R[1] + G[2] * R[2]));
+                /* per-brick adjoint, back to front */
+                double lamT = -gA;
+                for (int k = first[j + 1] - 1; k >= first[j]; --k) {
+                    const double *c = rec[k].rgba;
+                    double a = c[3], Tkk = Tk[k];
+                    double gdotc = gC[0] * c[0] + gC[1] * c[1] + gC[2] * c[2];
+                    double g[4] = {gC[0] * Tkk * a, gC[1] * Tkk * a, gC[2] * Tkk * a, Tkk * gdotc - Tkk * lamT};
+                    lamT = lamT * (1.0 - a) + a * gdotc;
+                    if (grad_tf) add_grad_tf(sc, grad_tf, rec[k].x, g);
+                    double u = (rec[k].s - sc->vmin) / (sc->vmax - sc->vmin);
+                    if (grad_vol && u > 0.0 && u < 1.0) {
+                        int i = (int)floor(rec[k].x);
+                        if (i > sc->ntf - 2) i = sc->ntf - 2;
+                        double ds = 0.0;
+                        for (int ch = 0; ch < 4; ++ch) ds += g[ch] * (tf_entry(sc, i + 1, ch) - tf_entry(sc, i, ch));
+                        add_grad_vol(sc, grad_vol, rec[k].p, ds * dxds);
+                    }
+                }
+                for (int ch = 0; ch < 3; ++ch) R[ch] = Cb[3 * j + ch] + (1.0 - Ab[j]) * R[ch];
+                Tb *= 1.0 - Ab[j];
+            }
+        }
+        free(rec); free(first); free(bid); free(Cb); free(Ab); free(Tk);
+    }
+    return fail == 0 ? 0 : (fail & 1 ? -1 : -4);
 }
 
 /* Point probes of the two per-sample stages, for function-level pins. */
