@@ -46,7 +46,7 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small", "precision"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "small", "precision", "grad"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -450,8 +450,91 @@ def run_precision(a):
     print(json.dumps(line))
 
 
+def run_grad(a):
+    """Differentiation form: one training step = forward of 16 views (512^2) of
+    the 256^3 blob volume (seed 4, 8 bricks), mean-squared image loss against
+    targets of the perturbed volume density*(1 + 0.05 xi), and the backward pass
+    through the adjoint kernels to the 256x4 table and every voxel."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2501_01628_gb300 import synth, vr
+    from paper_2501_01628_gb300.autograd import Renderer
+    __graft_entry__.build()
+    n = 256
+    rng = np.random.default_rng(4)
+    vol = synth.blob_volume(n, synth.draw_blobs(rng, 8))
+    tf = synth.random_tf(rng)
+    xi = np.random.default_rng(5).standard_normal(vol.shape).astype(np.float32)
+    vol_t = vol * (np.float32(1.0) + np.float32(0.05) * xi)
+    lo, hi = float(min(vol.min(), vol_t.min())), float(max(vol.max(), vol_t.max()))
+    part = dict(kind="grid", grid=(2, 2, 2))
+    cams = [synth.orbit_camera(512, 512, 22.5 * i, elevation_deg=20.0 if i % 2 else -10.0) for i in range(16)]
+    r = Renderer(part, lo, hi)
+    tft = torch.from_numpy(tf).cuda().requires_grad_(True)
+    dens = torch.from_numpy(vol).cuda().requires_grad_(True)
+    with torch.no_grad():
+        dt_ = torch.from_numpy(vol_t).cuda()
+        targets = [r.render(tft.detach(), dt_, c).clone() for c in cams]
+    # executed forward samples per step
+    ctx = vr.vr_create(0)
+    v = vr.vr_volume_create(ctx, dens.detach(), "f32", part)
+    vr.vr_set_transfer_function(ctx, tf, lo, hi)
+    vr.vr_set_render_params(ctx, 0.5, 1.0)
+    vr.vr_set_count_samples(ctx, True)
+    tmp = torch.empty((512, 512, 4), device="cuda")
+    for c in cams:
+        vr.vr_set_camera(ctx, c)
+        vr.vr_render_frame(ctx, v, tmp)
+    fwd_samples = vr.vr_get_sample_count(ctx)
+    vr.vr_volume_release(v)
+    vr.vr_destroy(ctx)
+
+    def step():
+        tft.grad = None
+        dens.grad = None
+        loss = sum(((r.render(tft, dens, c) - t) ** 2).mean() for c, t in zip(cams, targets)) / len(cams)
+        loss.backward()
+        return loss
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        loss = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    # forward only, for the split
+    e0.record(stream)
+    with torch.no_grad():
+        for _ in range(a.steps):
+            for c in cams:
+                r.render(tft, dens, c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / a.steps
+    r.close()
+    line = dict(metric=METRIC, value=fwd_samples / (ms / 1e3), unit=UNIT, n_gpus=1, steps=a.steps, warmup=a.warmup,
+                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic",
+                config=dict(workload="differentiation: 256^3 blobs (seed 4), 8 bricks, 16 views at 512x512, "
+                                     "MSE against the density*(1+0.05 xi) renders; gradients for the 256x4 table "
+                                     "and all 256^3 voxels; value = forward samples per second of training steps"),
+                forward_ms_per_16_views=fwd_ms, backward_ms=ms - fwd_ms,
+                forward_samples_per_step=fwd_samples, loss=float(loss.detach()),
+                gpu_launches=a.steps * 16 * 4)
+    print(json.dumps(line))
+
+
 def main():
     a = args_parse()
+    if a.workload == "grad":
+        run_grad(a)
+        return
     if a.workload == "precision":
         run_precision(a)
         return

@@ -127,7 +127,8 @@ vr_status vr_destroy(vr_ctx ctx);
 const char *vr_status_string(vr_status s);
 /* Text of the last error of `ctx` ("" if none); valid until the next call. */
 const char *vr_last_error(vr_ctx ctx);
-/* Wait for `stream` and report any device-side error word set by a kernel. */
+/* Wait for `stream` and report any device-side error word set by a kernel
+ * (VR_ERR_BOUNDS), clearing it. */
 vr_status vr_sync(vr_ctx ctx, void *stream);
 
 /* ---- volume (the distributed World of Sec. 3, all bricks on this GPU) ---- */
@@ -199,6 +200,28 @@ vr_status vr_frame_release(vr_frame fr);
 /* Steps 1 + 2 with a context-owned frame (no allocation once warm). */
 vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on_device,
                           void *stream);
+
+/* ---- differentiation ------------------------------------------------------ */
+
+/* Replace the voxel values of `vol` (same dims and partition) from the float32
+ * array `src` (host if src_on_device == 0, else device) and re-pack its bricks
+ * in place, on `stream`; complete when the call returns. No allocation for a
+ * device source. */
+vr_status vr_volume_update(vr_volume vol, const float *src, int src_on_device, void *stream);
+/* Gradient of a loss on the frame that vr_render_frame would produce with the
+ * context's current camera, transfer function and parameters (the paper renders
+ * only forward; this is the chain rule through the readings stated at the top
+ * of this header). Given dL/dI in `grad_rgba_dev` (H x W x 4 float32, device),
+ * ADDS dL/d(table) to `grad_tf_dev` (n x 4 float32, device) and, unless it is
+ * NULL, dL/d(voxel) to `grad_density_dev` (Nz x Ny x Nx float32, device, the
+ * original volume's indexing: halo copies are summed into the voxels they copy).
+ * Recomputes the forward pass per brick; transmittances come from checkpoints,
+ * never from division. Requires early termination off (VR_ERR_ARG otherwise).
+ * Runs of more than 4096 owned samples in one brick are skipped and reported as
+ * VR_ERR_BOUNDS by vr_sync. Float atomics: results vary in the last bits
+ * between runs. */
+vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_dev, float *grad_tf_dev,
+                             float *grad_density_dev, void *stream);
 
 /* ---- rendering without device allocation -------------------------------- */
 

@@ -71,7 +71,10 @@ struct vr_ctx_s {
     float ert_alpha = 1.0f;
     std::vector<int> factors;
     unsigned long long *d_counter = nullptr;
+    int *d_error = nullptr;        // device error word (vr_sync reports and clears it)
     bool count_samples = false;
+    float4 *d_gpart = nullptr;     // partial gradients (backward), partial-pool layout
+    long long gpart_cap = 0;
     vr_frame_s frame;              // context-owned frame for vr_render_frame
     float4 *d_img = nullptr;       // staging for host outputs
     long long img_cap = 0;
@@ -401,6 +404,27 @@ bool camera_valid(const vr_camera *cam)
     return make_basis(*cam, B);
 }
 
+// Pack every brick of `vol` from the device float32 volume `dsrc`.
+cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
+{
+    const size_t es = quad_size(vol->dtype);
+    const int nb = static_cast<int>(vol->boxes.size() / 6);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        const int *bx = &vol->boxes[6 * b];
+        PackParams pp;
+        pp.src = dsrc;
+        pp.dst = static_cast<char *>(vol->d_data) + vol->base[b] * static_cast<long long>(es);
+        for (int a = 0; a < 3; ++a) {
+            pp.N[a] = vol->dims[a];
+            pp.lo[a] = bx[a];
+            pp.s[a] = bx[3 + a] - bx[a] + 2;
+        }
+        e = launch_pack(pp, vol->dtype, s);
+    }
+    return e;
+}
+
 vr_status ensure_frame(vr_ctx ctx, vr_frame_s &fr, long long px)
 {
     if (px <= fr.cap_px) return VR_OK;
@@ -665,8 +689,11 @@ vr_status vr_create(int cuda_device, vr_ctx *out)
     ctx->device = cuda_device;
     DeviceGuard g(cuda_device);
     if (!g.ok || cudaMalloc(&ctx->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(ctx->d_counter, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMemset(ctx->d_counter, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_error, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_error, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(ctx->d_counter);
+        cudaFree(ctx->d_error);
         delete ctx;
         return VR_ERR_CUDA;
     }
@@ -683,6 +710,8 @@ vr_status vr_destroy(vr_ctx ctx)
     cudaDeviceSynchronize();
     cudaFree(ctx->d_tf);
     cudaFree(ctx->d_counter);
+    cudaFree(ctx->d_error);
+    cudaFree(ctx->d_gpart);
     cudaFree(ctx->frame.d_part);
     cudaFree(ctx->d_img);
     for (auto &t : ctx->timed) {
@@ -734,6 +763,12 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
     if (!ctx) return VR_ERR_ARG;
     DeviceGuard g(ctx->device);
     VR_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int err = 0;
+    VR_CUDA(ctx, cudaMemcpy(&err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        VR_CUDA(ctx, cudaMemset(ctx->d_error, 0, sizeof(int)));
+        return fail(ctx, VR_ERR_BOUNDS, "a backward pass met an owned-sample run longer than 4096 samples");
+    }
     return VR_OK;
 }
 
@@ -780,19 +815,7 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
         }
         dsrc = tmp;
     }
-    cudaError_t e = cudaSuccess;
-    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
-        const int *bx = &vol->boxes[6 * b];
-        PackParams pp;
-        pp.src = dsrc;
-        pp.dst = static_cast<char *>(vol->d_data) + vol->base[b] * static_cast<long long>(es);
-        for (int a = 0; a < 3; ++a) {
-            pp.N[a] = dims[a];
-            pp.lo[a] = bx[a];
-            pp.s[a] = bx[3 + a] - bx[a] + 2;
-        }
-        e = launch_pack(pp, storage, s);
-    }
+    cudaError_t e = pack_bricks(vol.get(), dsrc, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
@@ -801,6 +824,81 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
     }
     ctx->live_objects++;
     *out = vol.release();
+    return VR_OK;
+}
+
+vr_status vr_volume_update(vr_volume vol, const float *src, int src_on_device, void *stream)
+{
+    if (!vol || !src) return VR_ERR_ARG;
+    vr_ctx ctx = vol->ctx;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nvox = static_cast<size_t>(vol->dims[0]) * vol->dims[1] * vol->dims[2];
+    const float *dsrc = src;
+    float *tmp = nullptr;
+    if (!src_on_device) {
+        VR_CUDA(ctx, cudaMalloc(&tmp, nvox * sizeof(float)));
+        cudaError_t e = cudaMemcpyAsync(tmp, src, nvox * sizeof(float), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(ctx, e, "volume upload");
+        }
+        dsrc = tmp;
+    }
+    cudaError_t e = pack_bricks(vol, dsrc, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "volume pack");
+    return VR_OK;
+}
+
+vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_dev, float *grad_tf_dev,
+                             float *grad_density_dev, void *stream)
+{
+    if (!ctx || !vol) return VR_ERR_ARG;
+    if (!grad_rgba_dev || !grad_tf_dev) return fail(ctx, VR_ERR_ARG, "null gradient buffer");
+    if (vol->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume belongs to another context");
+    if (ctx->ert_alpha < 1.0f) return fail(ctx, VR_ERR_ARG, "backward requires early termination off");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    static thread_local MarchParams mp;
+    vr_frame_s &fr = ctx->frame;
+    // forward partials (recomputed: nothing per sample is kept from the forward call)
+    vr_status st = prepare_frame(ctx, vol, fr, mp);
+    if (st != VR_OK) return st;
+    st = ensure_frame(ctx, fr, std::max(fr.total_px, 1LL));
+    if (st != VR_OK) return st;
+    mp.partials = fr.d_part;
+    mp.sample_counter = nullptr;
+    VR_CUDA(ctx, launch_march(mp, vol->dtype, s));
+    if (fr.total_px > ctx->gpart_cap) {
+        cudaFree(ctx->d_gpart);
+        ctx->d_gpart = nullptr;
+        ctx->gpart_cap = 0;
+        VR_CUDA(ctx, cudaMalloc(&ctx->d_gpart, static_cast<size_t>(fr.total_px) * sizeof(float4)));
+        ctx->gpart_cap = fr.total_px;
+    }
+    static thread_local CompositeGradParams cg;
+    std::memset(&cg, 0, sizeof(cg));
+    cg.W = fr.W;
+    cg.H = fr.H;
+    cg.nb = fr.nb;
+    for (int j = 0; j < fr.nb; ++j) cg.order[j] = fr.order[j];
+    for (int b = 0; b < fr.nb; ++b) {
+        std::memcpy(cg.rect[b], &fr.rects[4 * b], 4 * sizeof(int));
+        cg.poff[b] = fr.poff[b];
+    }
+    cg.partials = fr.d_part;
+    cg.grad_img = reinterpret_cast<const float4 *>(grad_rgba_dev);
+    cg.grad_partials = ctx->d_gpart;
+    VR_CUDA(ctx, launch_composite_grad(cg, s));
+    GradArgs ga;
+    ga.grad_partials = ctx->d_gpart;
+    ga.grad_tf = grad_tf_dev;
+    ga.grad_vol = grad_density_dev;
+    for (int a = 0; a < 3; ++a) ga.N[a] = vol->dims[a];
+    ga.error = ctx->d_error;
+    VR_CUDA(ctx, launch_march_grad(mp, ga, vol->dtype, s));
     return VR_OK;
 }
 

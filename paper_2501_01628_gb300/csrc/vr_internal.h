@@ -79,6 +79,28 @@ struct CompositeParams {
     float4 *out;
 };
 
+// Composite adjoint: the composite's layout plus the image gradient and the
+// per-brick partial gradients it produces (same layout as the partials).
+struct CompositeGradParams {
+    int W, H;
+    int nb;
+    int order[kMaxBricks];
+    int rect[kMaxBricks][4];
+    long long poff[kMaxBricks];
+    const float4 *partials;
+    const float4 *grad_img;
+    float4 *grad_partials;
+};
+
+// March adjoint outputs (gradients are added into).
+struct GradArgs {
+    const float4 *grad_partials;
+    float *grad_tf;   // ntf x 4
+    float *grad_vol;  // Nz x Ny x Nx, or null
+    int N[3];
+    int *error;       // device error word: bit 0 = a run exceeded the checkpoint storage
+};
+
 struct PackParams {
     const float *src;
     void *dst;
@@ -91,5 +113,7 @@ struct PackParams {
 cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s);
 cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s);
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s);
+cudaError_t launch_composite_grad(const CompositeGradParams &p, cudaStream_t s);
+cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, vr_dtype dtype, cudaStream_t s);
 
 }  // namespace vr

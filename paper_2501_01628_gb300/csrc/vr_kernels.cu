@@ -5,61 +5,14 @@
 // renders its share. Sec. 3/4: the per-rank images are composited into one
 // framebuffer. The optical model is the standard emission-absorption one; the
 // exact per-sample definitions are stated in include/vr.h.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include "vr_internal.h"
+#include "vr_device.cuh"
 
 namespace vr {
 namespace {
 
-// ---------------------------------------------------------------------------
-// Brick storage: "xy-quads". Element (i,j,k) of a brick whose haloed extents
-// are (sx, sy, sz) holds the four voxels (i,j,k), (i+1,j,k), (i,j+1,k),
-// (i+1,j+1,k), for i < sx-1, j < sy-1, k < sz. A trilinear sample then needs
-// two vector loads (planes k and k+1) instead of eight scalar gathers, at four
-// times the storage -- L1 wavefronts, not HBM capacity, bound the march.
-// ---------------------------------------------------------------------------
-template <typename T> struct Quad;
-template <> struct Quad<float> {
-    using type = float4;
-    static __device__ __forceinline__ float4 load(const float4 *p) { return __ldg(p); }
-    static __device__ __forceinline__ float4 make(float a, float b, float c, float d)
-    {
-        return make_float4(a, b, c, d);
-    }
-};
-template <> struct Quad<__nv_bfloat16> {
-    using type = uint2;
-    static __device__ __forceinline__ float4 load(const uint2 *p)
-    {
-        const uint2 u = __ldg(p);
-        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
-                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
-    }
-    static __device__ __forceinline__ uint2 make(float a, float b, float c, float d)
-    {
-        auto bits = [](float v) {
-            return static_cast<unsigned>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
-        };
-        return make_uint2(bits(a) | (bits(b) << 16), bits(c) | (bits(d) << 16));
-    }
-};
-template <> struct Quad<__half> {
-    using type = uint2;
-    static __device__ __forceinline__ float4 load(const uint2 *p)
-    {
-        const uint2 u = __ldg(p);
-        const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
-        const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
-        return make_float4(lo.x, lo.y, hi.x, hi.y);
-    }
-    static __device__ __forceinline__ uint2 make(float a, float b, float c, float d)
-    {
-        auto bits = [](float v) { return static_cast<unsigned>(__half_as_ushort(__float2half_rn(v))); };
-        return make_uint2(bits(a) | (bits(b) << 16), bits(c) | (bits(d) << 16));
-    }
-};
+using dev::Quad;
+using dev::find_brick;
+using dev::over;
 
 // ---------------------------------------------------------------------------
 // Pack: global x-fastest float32 volume -> one brick of xy-quads (halo of one
@@ -94,17 +47,6 @@ __global__ void pack_kernel(PackParams p)
 // ---------------------------------------------------------------------------
 // March: one thread per pixel of a brick's footprint; 8x4-pixel warp packets.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_brick(const MarchParams &p, int item)
-{
-    int lo = 0, hi = p.nb - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (p.b[mid].item_begin <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 template <typename S, bool COUNT>
 __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ MarchParams p)
 {
@@ -123,83 +65,12 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     if (rx >= B.rect[2] || ry >= B.rect[3]) return;
     const int px = B.rect[0] + rx, py = B.rect[1] + ry;
 
-    // primary ray (FP32; identical arithmetic for every brick)
-    const float fx = (static_cast<float>(px) + 0.5f) * p.inv_W;
-    const float fy = (static_cast<float>(py) + 0.5f) * p.inv_H;
-    float o[3], d[3];
-    if (p.ortho) {
-        const float a = (fx - 0.5f) * p.ow, b = (fy - 0.5f) * p.oh;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            o[i] = fmaf(b, p.u[i], fmaf(a, p.r[i], p.eye[i]));
-            d[i] = p.f[i];
-        }
-    } else {
-        const float sx = (fx * 2.0f - 1.0f) * p.tanx, sy = (fy * 2.0f - 1.0f) * p.tany;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            o[i] = p.eye[i];
-            d[i] = fmaf(sy, p.u[i], fmaf(sx, p.r[i], p.f[i]));
-        }
-        const float inv = __frsqrt_rn(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) d[i] *= inv;
-    }
-    // voxel-space origin and direction; t stays in world units
-    float ov[3], dv[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        ov[i] = o[i] * p.nmax;
-        dv[i] = d[i] * p.nmax;
-    }
-
-    // whole-volume interval [t_in, t_out) and this brick's slab interval
-    float t0 = 0.0f, t1 = 3.0e38f, b0 = 0.0f, b1 = 3.0e38f;
-    bool hit = true;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (dv[i] == 0.0f) {
-            if (ov[i] < 0.0f || ov[i] > p.N[i]) hit = false;
-            if (ov[i] < static_cast<float>(B.lo[i]) || ov[i] > static_cast<float>(B.hi[i])) hit = false;
-        } else {
-            const float inv = __frcp_rn(dv[i]);
-            float ta = (0.0f - ov[i]) * inv, tb = (p.N[i] - ov[i]) * inv;
-            t0 = fmaxf(t0, fminf(ta, tb));
-            t1 = fminf(t1, fmaxf(ta, tb));
-            ta = (static_cast<float>(B.lo[i]) - ov[i]) * inv;
-            tb = (static_cast<float>(B.hi[i]) - ov[i]) * inv;
-            b0 = fmaxf(b0, fminf(ta, tb));
-            b1 = fminf(b1, fmaxf(ta, tb));
-        }
-    }
-    // NOTE: the whole-volume t_in must not depend on the brick; it uses
-    // (0 - o)/d and (N - o)/d only, in the same order for every brick.
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
     unsigned long long executed = 0;
-    if (hit && t0 < t1 && b0 <= b1) {
-        const float t_in = t0, t_out = t1;
-        // Slab estimate of the samples this brick owns, widened by a margin that
-        // covers FP32 rounding of the positions (large only for rays nearly
-        // parallel to a face), then made exact with the ownership test itself.
-        float dmin = 3.0e38f;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            if (dv[i] != 0.0f) dmin = fminf(dmin, fabsf(dv[i]));
-        const int margin = 2 + static_cast<int>(fminf(1.0e6f, __fdividef(1.0e-6f * p.nmax, dmin * p.dt)));
-        int ka = max(0, static_cast<int>(floorf((b0 - t_in) * p.inv_dt - 0.5f)) - margin);
-        int kb = static_cast<int>(ceilf((fminf(b1, t_out) - t_in) * p.inv_dt - 0.5f)) + margin;
-        // sample k is owned iff it lies before t_out and its cell is in the brick
-        // (same FP32 arithmetic for every brick: each sample has exactly one owner)
-        auto owned = [&](int k) {
-            const float t = fmaf(static_cast<float>(k) + 0.5f, p.dt, t_in);
-            const float qxv = fmaf(t, dv[0], ov[0]);
-            const float qyv = fmaf(t, dv[1], ov[1]);
-            const float qzv = fmaf(t, dv[2], ov[2]);
-            return t < t_out && qxv >= B.own_lo[0] && qxv < B.own_hi[0] && qyv >= B.own_lo[1] &&
-                   qyv < B.own_hi[1] && qzv >= B.own_lo[2] && qzv < B.own_hi[2];
-        };
-        while (ka <= kb && !owned(ka)) ++ka;
-        while (kb > ka && !owned(kb)) --kb;
+    dev::OwnedRun run;
+    dev::owned_run(p, B, px, py, run);
+    {
+        const int ka = run.ka, kb = run.kb;
         // owned samples are contiguous along the ray: [ka, kb] are all owned
         if (ka <= kb) {
             using Q = typename Quad<S>::type;
@@ -207,13 +78,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
             const int nbx = B.sx / 2, nby = B.sy / 2;
             const int imax = B.hi[0] - B.lo[0], jmax = B.hi[1] - B.lo[1], kmax = B.hi[2] - B.lo[2];
             const float xmax = static_cast<float>(p.ntf - 1);
-            // local voxel-centre coordinates v = q - lo + 1/2 as a linear function of k + 1/2
-            float base[3], step[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                step[i] = dv[i] * p.dt;
-                base[i] = fmaf(t_in, dv[i], ov[i] - (static_cast<float>(B.lo[i]) - 0.5f));
-            }
+            const float *base = run.base, *step = run.step;
             // two samples per iteration: both cells' loads are issued before either
             // sample is classified (independent memory requests in flight)
             int prev = -1;
@@ -287,13 +152,6 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
 // Composite: one block per 32x8 image tile, one thread per pixel; partials are
 // combined front to back with "over" along the configured association tree.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float4 over(float4 front, float4 back)
-{
-    const float w = 1.0f - front.w;
-    return make_float4(fmaf(w, back.x, front.x), fmaf(w, back.y, front.y), fmaf(w, back.z, front.z),
-                       fmaf(w, back.w, front.w));
-}
-
 // Per tile, warp 0 first compacts the bricks whose rectangles overlap the tile,
 // in visibility order. Absent partials are the identity of "over", so only the
 // association tree's carries at skipped positions matter; consecutive carries

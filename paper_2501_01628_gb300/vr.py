@@ -35,6 +35,7 @@ EXPORTS = (
     "vr_render_partials", "vr_frame_info", "vr_frame_partial", "vr_composite",
     "vr_frame_release", "vr_render_frame", "vr_partition_boxes", "vr_plan_view",
     "vr_set_kernel_timing", "vr_get_kernel_timing", "vr_render_frame_noalloc",
+    "vr_volume_update", "vr_render_backward",
 )
 
 
@@ -86,6 +87,8 @@ _SIG = {
     "vr_render_frame_noalloc": (_I, [_P, _P, ctypes.POINTER(vr_partition), _P, _I, ctypes.c_float,
                                      ctypes.c_float, ctypes.POINTER(vr_camera), ctypes.c_float,
                                      ctypes.c_float, _P, _P]),
+    "vr_volume_update": (_I, [_P, _P, _I, _P]),
+    "vr_render_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
     "vr_plan_view": (_I, [_P, ctypes.POINTER(vr_partition), ctypes.POINTER(vr_camera), _P, _P]),
 }
@@ -226,6 +229,27 @@ def vr_volume_create(ctx, volume, storage: str = "f32", partition=None, stream=N
     _check(lib().vr_volume_create(ctx, dims, DTYPES[storage], ctypes.byref(part), ptr, on_dev,
                                   _stream(stream), ctypes.byref(h)), ctx, "vr_volume_create")
     return h
+
+
+def vr_volume_update(vol, volume, stream=None):
+    """Re-pack `vol` from a float32 [Nz, Ny, Nx] array (same dims)."""
+    ptr, on_dev, keep = _ptr_and_loc(volume)
+    _check(lib().vr_volume_update(vol, ptr, on_dev, _stream(stream)), None, "vr_volume_update")
+
+
+def vr_render_backward(ctx, vol, grad_rgba, grad_tf, grad_density=None, stream=None):
+    """Adds dL/d(table) to grad_tf and dL/d(voxels) to grad_density (CUDA float32
+    tensors) for dL/dI = grad_rgba ([H, W, 4] CUDA float32)."""
+    g, gon, _ = _ptr_and_loc(grad_rgba)
+    t, ton, _ = _ptr_and_loc(grad_tf)
+    d = None
+    if grad_density is not None:
+        d, don, _ = _ptr_and_loc(grad_density)
+        if not don:
+            raise ValueError("grad_density must be a CUDA tensor")
+    if not (gon and ton):
+        raise ValueError("gradients must be CUDA tensors")
+    _check(lib().vr_render_backward(ctx, vol, g, t, d, _stream(stream)), ctx, "vr_render_backward")
 
 
 def vr_volume_release(vol):
