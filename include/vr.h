@@ -52,6 +52,7 @@ extern "C" {
 typedef struct vr_ctx_s *vr_ctx;
 typedef struct vr_volume_s *vr_volume;
 typedef struct vr_frame_s *vr_frame;
+typedef struct vr_batch_s *vr_batch;
 
 typedef enum {
     VR_OK = 0,
@@ -128,7 +129,8 @@ const char *vr_status_string(vr_status s);
 /* Text of the last error of `ctx` ("" if none); valid until the next call. */
 const char *vr_last_error(vr_ctx ctx);
 /* Wait for `stream` and report any device-side error word set by a kernel
- * (VR_ERR_BOUNDS), clearing it. */
+ * (VR_ERR_TIMEOUT for a bounded wait that gave up, VR_ERR_BOUNDS for an
+ * adjoint run beyond its checkpoint storage), clearing it. */
 vr_status vr_sync(vr_ctx ctx, void *stream);
 
 /* ---- volume (the distributed World of Sec. 3, all bricks on this GPU) ---- */
@@ -200,6 +202,40 @@ vr_status vr_frame_release(vr_frame fr);
 /* Steps 1 + 2 with a context-owned frame (no allocation once warm). */
 vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on_device,
                           void *stream);
+
+/* ---- batched form: many renders in one launch ------------------------------ */
+
+/* A batch renders every (volume, view) pair -- render r = v * n_views + w --
+ * into out_rgba_dev (n_volumes x n_views x H x W x 4 float32, device), e.g. the
+ * time steps and fields of a time-varying data set (Sec. 4) seen from many
+ * views (replication of resident data, Sec. 2.2). All renders and their
+ * compositing run in ONE persistent, cooperative kernel, captured with its
+ * counter resets in a CUDA graph; vr_batch_launch replays that graph.
+ *   - volumes: same dims, partition and storage type; per-volume classification
+ *     range vmins/vmaxs (NULL: the context's range); the context's transfer
+ *     function table, step and early termination are captured at creation;
+ *   - cameras: same image size; direct (non-radix) front-to-back composite;
+ *   - work items (the (brick, tile) march items of render r, then its composite
+ *     tiles) are claimed in order from one counter; partial images live in a
+ *     ring of slots reused once composited; device-side waits are bounded and
+ *     report VR_ERR_TIMEOUT through vr_sync instead of hanging.
+ * The batch belongs to the library until vr_batch_release. */
+vr_status vr_batch_create(vr_ctx ctx, int n_volumes, const vr_volume *vols, const float *vmins, const float *vmaxs,
+                          int n_views, const vr_camera *cams, float *out_rgba_dev, vr_batch *out);
+/* Launch the whole batch on `stream` (asynchronous). */
+vr_status vr_batch_launch(vr_batch batch, void *stream);
+/* Time the candidates -- work order (0: render by render; 1: volume by volume
+ * with every view marching one brick before the next, so the brick stays in L2),
+ * ray-packet shape (4x8, 8x4, 16x2 pixels per warp) and resident blocks per SM --
+ * with one launch each (synchronous) and keep the fastest; with a non-NULL
+ * cache_path the choice is read from / appended to a text cache keyed by device
+ * name and batch shape. chosen (may be NULL, else 4 ints) gets {packet width,
+ * blocks per SM, ring slots, work order}. */
+vr_status vr_batch_autotune(vr_batch batch, void *stream, const char *cache_path, int *chosen);
+/* Set the configuration directly: packet_width 4, 8 or 16; blocks_per_sm (0 =
+ * as many as fit); order 0 or 1 as for vr_batch_autotune. */
+vr_status vr_batch_configure(vr_batch batch, int packet_width, int blocks_per_sm, int order);
+vr_status vr_batch_release(vr_batch batch);
 
 /* ---- differentiation ------------------------------------------------------ */
 

@@ -78,7 +78,8 @@ struct OwnedRun {
     int ka, kb;
 };
 
-__device__ __forceinline__ void owned_run(const MarchParams &p, const BrickLaunch &B, int px, int py, OwnedRun &run)
+template <typename P>
+__device__ __forceinline__ void owned_run(const P &p, const BrickLaunch &B, int px, int py, OwnedRun &run)
 {
     run.ka = 0;
     run.kb = -1;
@@ -165,6 +166,94 @@ __device__ __forceinline__ void owned_run(const MarchParams &p, const BrickLaunc
             run.base[i] = fmaf(t_in, dv[i], ov[i] - (static_cast<float>(B.lo[i]) - 0.5f));
         }
     }
+}
+
+// Front-to-back emission-absorption over one owned run (see include/vr.h):
+// C += T alpha rgb, T *= (1 - alpha), with the two samples of an iteration
+// requesting their cells' quads before either is classified, and a sample in
+// the previous sample's cell reusing its quads. Returns the partial (C, 1 - T).
+template <typename S, bool COUNT>
+__device__ __forceinline__ float4 march_run(const void *data, const BrickLaunch &B, const OwnedRun &run,
+                                            const float4 *tf, float tf_scale, float tf_bias, int ntf, float ert_T,
+                                            unsigned long long &executed)
+{
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+    {
+        const int ka = run.ka, kb = run.kb;
+        // owned samples are contiguous along the ray: [ka, kb] are all owned
+        if (ka <= kb) {
+            using Q = typename Quad<S>::type;
+            const Q *vox = static_cast<const Q *>(data) + B.base;
+            const int nbx = B.sx / 2, nby = B.sy / 2;
+            const int imax = B.hi[0] - B.lo[0], jmax = B.hi[1] - B.lo[1], kmax = B.hi[2] - B.lo[2];
+            const float xmax = static_cast<float>(ntf - 1);
+            const float *base = run.base, *step = run.step;
+            // two samples per iteration: both cells' loads are issued before either
+            // sample is classified (independent memory requests in flight)
+            int prev = -1;
+            float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+            float kh = static_cast<float>(ka) + 0.5f;
+            // quad indices of planes k and k+1 of the sample's cell; the clamps
+            // only guard memory (owned samples always lie inside the brick)
+            auto locate = [&](float h, int &cell, int &cell1, float &wx, float &wy, float &wz) {
+                const float vx = fmaf(h, step[0], base[0]);
+                const float vy = fmaf(h, step[1], base[1]);
+                const float vz = fmaf(h, step[2], base[2]);
+                const float flx = floorf(vx), fly = floorf(vy), flz = floorf(vz);
+                wx = vx - flx;
+                wy = vy - fly;
+                wz = vz - flz;
+                const int i = min(max(static_cast<int>(flx), 0), imax);
+                const int j = min(max(static_cast<int>(fly), 0), jmax);
+                const int k = min(max(static_cast<int>(flz), 0), kmax);
+                cell = quad_index(i, j, k, nbx, nby);
+                cell1 = quad_index(i, j, k + 1, nbx, nby);
+            };
+            auto shade = [&](const float4 &a0, const float4 &a1, float wx, float wy, float wz) {
+                const float c00 = fmaf(wx, a0.y - a0.x, a0.x), c10 = fmaf(wx, a0.w - a0.z, a0.z);
+                const float c01 = fmaf(wx, a1.y - a1.x, a1.x), c11 = fmaf(wx, a1.w - a1.z, a1.z);
+                const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
+                const float s = fmaf(wz, c1 - c0, c0);
+                const float x = fminf(fmaxf(fmaf(s, tf_scale, tf_bias), 0.0f), xmax);
+                const int ti = static_cast<int>(x);
+                const float w = x - static_cast<float>(ti);
+                const float4 e0 = __ldg(tf + 2 * ti), de = __ldg(tf + 2 * ti + 1);
+                const float r = fmaf(w, de.x, e0.x), g = fmaf(w, de.y, e0.y);
+                const float bb = fmaf(w, de.z, e0.z), al = fmaf(w, de.w, e0.w);
+                const float ta = T * al;
+                C0 = fmaf(ta, r, C0);
+                C1 = fmaf(ta, g, C1);
+                C2 = fmaf(ta, bb, C2);
+                T = T - ta;
+            };
+            for (int k = ka; k <= kb; k += 2, kh += 2.0f) {
+                int ca, ca1, cb, cb1;
+                float ax, ay, az, bx, by, bz;
+                locate(kh, ca, ca1, ax, ay, az);
+                const bool two = k < kb;
+                locate(kh + 1.0f, cb, cb1, bx, by, bz);
+                if (ca != prev) {
+                    q0 = Quad<S>::load(vox + ca);
+                    q1 = Quad<S>::load(vox + ca1);
+                }
+                float4 r0 = q0, r1 = q1;
+                if (two && cb != ca) {
+                    r0 = Quad<S>::load(vox + cb);
+                    r1 = Quad<S>::load(vox + cb1);
+                }
+                shade(q0, q1, ax, ay, az);
+                if (COUNT) ++executed;
+                if (T <= ert_T || !two) break;
+                shade(r0, r1, bx, by, bz);
+                if (COUNT) ++executed;
+                if (T <= ert_T) break;
+                q0 = r0;
+                q1 = r1;
+                prev = cb;
+            }
+        }
+    }
+    return make_float4(C0, C1, C2, 1.0f - T);
 }
 
 __device__ __forceinline__ float4 over(float4 front, float4 back)

@@ -15,92 +15,13 @@
 #include <string>
 #include <vector>
 
-#include "vr_internal.h"
+#include "vr_objects.h"
 
 using namespace vr;
+using namespace vr::host;
 
-namespace {
-
-struct KdNode {
-    int axis = -1;  // -1: leaf
-    int cut = 0;    // voxel plane
-    int child[2] = {-1, -1};
-    int brick = -1;
-};
-
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-}  // namespace
-
-struct vr_frame_s {
-    vr_ctx ctx = nullptr;
-    int nb = 0;
-    int W = 0, H = 0;
-    std::vector<int> rects;        // nb x 4
-    std::vector<int> order;        // nb
-    std::vector<long long> poff;   // nb, float4 units
-    long long total_px = 0;
-    float4 *d_part = nullptr;
-    long long cap_px = 0;
-    bool owned_by_ctx = false;
-};
-
-struct vr_ctx_s {
-    int device = 0;
-    std::string last_error;
-    float4 *d_tf = nullptr;
-    int ntf = 0;
-    int tf_cap = 0;
-    float vmin = 0.f, vmax = 1.f;
-    bool has_tf = false;
-    vr_camera cam{};
-    bool has_cam = false;
-    float step = 0.5f;
-    float ert_alpha = 1.0f;
-    std::vector<int> factors;
-    unsigned long long *d_counter = nullptr;
-    int *d_error = nullptr;        // device error word (vr_sync reports and clears it)
-    bool count_samples = false;
-    float4 *d_gpart = nullptr;     // partial gradients (backward), partial-pool layout
-    long long gpart_cap = 0;
-    vr_frame_s frame;              // context-owned frame for vr_render_frame
-    float4 *d_img = nullptr;       // staging for host outputs
-    long long img_cap = 0;
-    int live_objects = 0;
-    // kernel timing (vr_set_kernel_timing)
-    bool timing = false;
-    struct Timed {
-        cudaEvent_t a, b;
-        int kind;  // 0 march, 1 composite
-    };
-    std::vector<Timed> timed;
-    std::vector<cudaEvent_t> event_pool;
-};
-
-struct vr_volume_s {
-    vr_ctx ctx = nullptr;
-    int dims[3] = {0, 0, 0};
-    vr_dtype dtype = VR_F32;
-    std::vector<int> boxes;        // nb x 6
-    std::vector<long long> base;   // element offsets
-    std::vector<KdNode> tree;      // node 0 = root
-    void *d_data = nullptr;
-    long long bytes = 0;
-};
-
-namespace {
+namespace vr {
+namespace host {
 
 size_t elem_size(vr_dtype t) { return t == VR_F32 ? 4 : 2; }
 // bytes of one xy-quad (four voxels) in device storage
@@ -125,12 +46,6 @@ vr_status cuda_fail(vr_ctx ctx, cudaError_t e, const char *what)
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
     return fail(ctx, e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA, m);
 }
-
-#define VR_CUDA(ctx, call)                                   \
-    do {                                                     \
-        cudaError_t e_ = (call);                             \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
-    } while (0)
 
 int nmax3(const int d[3]) { return std::max(d[0], std::max(d[1], d[2])); }
 
@@ -255,11 +170,6 @@ void visibility_order(const std::vector<KdNode> &tree, int node, const vr_camera
     visibility_order(tree, n.child[low_first ? 0 : 1], cam, nmax, out);
     visibility_order(tree, n.child[low_first ? 1 : 0], cam, nmax, out);
 }
-
-struct Basis {
-    double f[3], r[3], u[3];
-    double tanx, tany;
-};
 
 void normalize(double v[3])
 {
@@ -621,7 +531,8 @@ vr_status composite_to(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device
     return VR_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace vr
 
 // ===========================================================================
 // C ABI
@@ -767,6 +678,7 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
     VR_CUDA(ctx, cudaMemcpy(&err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         VR_CUDA(ctx, cudaMemset(ctx->d_error, 0, sizeof(int)));
+        if (err & 2) return fail(ctx, VR_ERR_TIMEOUT, "a bounded device-side wait of the batched kernel gave up");
         return fail(ctx, VR_ERR_BOUNDS, "a backward pass met an owned-sample run longer than 4096 samples");
     }
     return VR_OK;

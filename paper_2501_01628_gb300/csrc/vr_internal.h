@@ -101,6 +101,56 @@ struct GradArgs {
     int *error;       // device error word: bit 0 = a run exceeded the checkpoint storage
 };
 
+// Batched form: per view, the camera fields that dev::owned_run reads (same
+// names as MarchParams) and the view's work-item counts.
+struct BatchView {
+    float eye[3], r[3], u[3], f[3];
+    float tanx, tany;
+    float ow, oh;
+    int ortho;
+    int W, H;
+    float inv_W, inv_H;
+    float nmax;
+    float N[3];
+    float dt, inv_dt;
+    int march_items;  // (brick, tile) items of one render of this view
+    int comp_items;   // composite tiles of one render of this view
+};
+
+constexpr int kBatchCompW = 16;  // composite tile of the batched kernel (128 threads)
+constexpr int kBatchCompH = 8;
+
+struct BatchParams {
+    int n_renders, n_views, nb;
+    int mode;                        // 0: unit = one render; 1: unit = one volume, all views, brick-major
+    int n_units;
+    const int *unit_march;           // per unit: march items
+    const int *unit_comp;            // per unit: composite tiles
+    const long long *bw_begin;       // mode 1: nb x n_views + 1 tile offsets, (brick, view) order
+    long long view_stride;           // mode 1: partial pixels per view inside a unit's ring slot
+    int pw;                          // ray-packet width: a warp marches pw x (32/pw) pixels
+    long long total_items;
+    const long long *render_begin;   // n_units + 2 segment starts: segment g = march items of
+                                     // unit g, then composite tiles of unit g-1
+    const BatchView *views;          // n_views
+    const BrickLaunch *vb;           // n_views x nb; rect/poff/item_begin/tiles_x per view
+    const int *order;                // n_views x nb, front to back
+    const void *const *vol_data;     // per volume: brick storage
+    const float2 *vol_tf;            // per volume: (tf_scale, tf_bias)
+    const float4 *tf;                // (T, dT) pairs
+    int ntf;
+    float ert_T;
+    float4 *ring;                    // slots x slot_px partial pixels
+    long long slot_px;               // partial pixels per ring slot (one unit)
+    int slots;
+    float4 *out;                     // n_renders x H x W
+    unsigned long long *claim;       // work counter
+    int *march_done;                 // per unit: finished march items
+    int *comp_done;                  // per unit: finished composite tiles
+    int *error;                      // bit 1: a bounded wait gave up
+    int wait_limit;                  // spin iterations (about 128 ns each) before giving up
+};
+
 struct PackParams {
     const float *src;
     void *dst;
@@ -115,5 +165,8 @@ cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s);
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s);
 cudaError_t launch_composite_grad(const CompositeGradParams &p, cudaStream_t s);
 cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, vr_dtype dtype, cudaStream_t s);
+// Persistent batched kernel: cooperative launch of `blocks` blocks of 128 threads.
+cudaError_t launch_batch(const BatchParams &p, vr_dtype dtype, int blocks, cudaStream_t s);
+int batch_max_blocks_per_sm(vr_dtype dtype);
 
 }  // namespace vr

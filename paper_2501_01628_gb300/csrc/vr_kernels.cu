@@ -65,86 +65,11 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     if (rx >= B.rect[2] || ry >= B.rect[3]) return;
     const int px = B.rect[0] + rx, py = B.rect[1] + ry;
 
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
     unsigned long long executed = 0;
     dev::OwnedRun run;
     dev::owned_run(p, B, px, py, run);
-    {
-        const int ka = run.ka, kb = run.kb;
-        // owned samples are contiguous along the ray: [ka, kb] are all owned
-        if (ka <= kb) {
-            using Q = typename Quad<S>::type;
-            const Q *vox = static_cast<const Q *>(p.data) + B.base;
-            const int nbx = B.sx / 2, nby = B.sy / 2;
-            const int imax = B.hi[0] - B.lo[0], jmax = B.hi[1] - B.lo[1], kmax = B.hi[2] - B.lo[2];
-            const float xmax = static_cast<float>(p.ntf - 1);
-            const float *base = run.base, *step = run.step;
-            // two samples per iteration: both cells' loads are issued before either
-            // sample is classified (independent memory requests in flight)
-            int prev = -1;
-            float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
-            float kh = static_cast<float>(ka) + 0.5f;
-            // quad indices of planes k and k+1 of the sample's cell; the clamps
-            // only guard memory (owned samples always lie inside the brick)
-            auto locate = [&](float h, int &cell, int &cell1, float &wx, float &wy, float &wz) {
-                const float vx = fmaf(h, step[0], base[0]);
-                const float vy = fmaf(h, step[1], base[1]);
-                const float vz = fmaf(h, step[2], base[2]);
-                const float flx = floorf(vx), fly = floorf(vy), flz = floorf(vz);
-                wx = vx - flx;
-                wy = vy - fly;
-                wz = vz - flz;
-                const int i = min(max(static_cast<int>(flx), 0), imax);
-                const int j = min(max(static_cast<int>(fly), 0), jmax);
-                const int k = min(max(static_cast<int>(flz), 0), kmax);
-                cell = quad_index(i, j, k, nbx, nby);
-                cell1 = quad_index(i, j, k + 1, nbx, nby);
-            };
-            auto shade = [&](const float4 &a0, const float4 &a1, float wx, float wy, float wz) {
-                const float c00 = fmaf(wx, a0.y - a0.x, a0.x), c10 = fmaf(wx, a0.w - a0.z, a0.z);
-                const float c01 = fmaf(wx, a1.y - a1.x, a1.x), c11 = fmaf(wx, a1.w - a1.z, a1.z);
-                const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
-                const float s = fmaf(wz, c1 - c0, c0);
-                const float x = fminf(fmaxf(fmaf(s, p.tf_scale, p.tf_bias), 0.0f), xmax);
-                const int ti = static_cast<int>(x);
-                const float w = x - static_cast<float>(ti);
-                const float4 e0 = __ldg(p.tf + 2 * ti), de = __ldg(p.tf + 2 * ti + 1);
-                const float r = fmaf(w, de.x, e0.x), g = fmaf(w, de.y, e0.y);
-                const float bb = fmaf(w, de.z, e0.z), al = fmaf(w, de.w, e0.w);
-                const float ta = T * al;
-                C0 = fmaf(ta, r, C0);
-                C1 = fmaf(ta, g, C1);
-                C2 = fmaf(ta, bb, C2);
-                T = T - ta;
-            };
-            for (int k = ka; k <= kb; k += 2, kh += 2.0f) {
-                int ca, ca1, cb, cb1;
-                float ax, ay, az, bx, by, bz;
-                locate(kh, ca, ca1, ax, ay, az);
-                const bool two = k < kb;
-                locate(kh + 1.0f, cb, cb1, bx, by, bz);
-                if (ca != prev) {
-                    q0 = Quad<S>::load(vox + ca);
-                    q1 = Quad<S>::load(vox + ca1);
-                }
-                float4 r0 = q0, r1 = q1;
-                if (two && cb != ca) {
-                    r0 = Quad<S>::load(vox + cb);
-                    r1 = Quad<S>::load(vox + cb1);
-                }
-                shade(q0, q1, ax, ay, az);
-                if (COUNT) ++executed;
-                if (T <= p.ert_T || !two) break;
-                shade(r0, r1, bx, by, bz);
-                if (COUNT) ++executed;
-                if (T <= p.ert_T) break;
-                q0 = r0;
-                q1 = r1;
-                prev = cb;
-            }
-        }
-    }
-    p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = make_float4(C0, C1, C2, 1.0f - T);
+    const float4 c = dev::march_run<S, COUNT>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, executed);
+    p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = c;
     if (COUNT && executed) atomicAdd(p.sample_counter, executed);
 }
 

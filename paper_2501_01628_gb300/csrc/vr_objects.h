@@ -1,0 +1,119 @@
+// vr_objects.h -- host-side objects of libvr (context, volume, frame) and the
+// host helpers shared by vr_host.cpp and vr_batch.cu. Not part of the public ABI.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "vr_internal.h"
+
+namespace vr {
+namespace host {
+
+struct KdNode {
+    int axis = -1;  // -1: leaf
+    int cut = 0;    // voxel plane
+    int child[2] = {-1, -1};
+    int brick = -1;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace host
+}  // namespace vr
+
+struct vr_frame_s {
+    vr_ctx ctx = nullptr;
+    int nb = 0;
+    int W = 0, H = 0;
+    std::vector<int> rects;        // nb x 4
+    std::vector<int> order;        // nb
+    std::vector<long long> poff;   // nb, float4 units
+    long long total_px = 0;
+    float4 *d_part = nullptr;
+    long long cap_px = 0;
+    bool owned_by_ctx = false;
+};
+
+struct vr_ctx_s {
+    int device = 0;
+    std::string last_error;
+    float4 *d_tf = nullptr;
+    int ntf = 0;
+    int tf_cap = 0;
+    float vmin = 0.f, vmax = 1.f;
+    bool has_tf = false;
+    vr_camera cam{};
+    bool has_cam = false;
+    float step = 0.5f;
+    float ert_alpha = 1.0f;
+    std::vector<int> factors;
+    unsigned long long *d_counter = nullptr;
+    int *d_error = nullptr;        // device error word (vr_sync reports and clears it)
+    bool count_samples = false;
+    float4 *d_gpart = nullptr;     // partial gradients (backward), partial-pool layout
+    long long gpart_cap = 0;
+    vr_frame_s frame;              // context-owned frame for vr_render_frame
+    float4 *d_img = nullptr;       // staging for host outputs
+    long long img_cap = 0;
+    int live_objects = 0;
+    // kernel timing (vr_set_kernel_timing)
+    bool timing = false;
+    struct Timed {
+        cudaEvent_t a, b;
+        int kind;  // 0 march, 1 composite
+    };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+struct vr_volume_s {
+    vr_ctx ctx = nullptr;
+    int dims[3] = {0, 0, 0};
+    vr_dtype dtype = VR_F32;
+    std::vector<int> boxes;        // nb x 6
+    std::vector<long long> base;   // element offsets
+    std::vector<vr::host::KdNode> tree;  // node 0 = root
+    void *d_data = nullptr;
+    long long bytes = 0;
+};
+
+namespace vr {
+namespace host {
+
+size_t elem_size(vr_dtype t);
+size_t quad_size(vr_dtype t);
+long long brick_quads(const int *bx);
+vr_status fail(vr_ctx ctx, vr_status s, const std::string &msg);
+vr_status cuda_fail(vr_ctx ctx, cudaError_t e, const char *what);
+int nmax3(const int d[3]);
+void visibility_order(const std::vector<KdNode> &tree, int node, const vr_camera &cam, double nmax,
+                      std::vector<int> &out);
+struct Basis {
+    double f[3], r[3], u[3];
+    double tanx, tany;
+};
+bool make_basis(const vr_camera &c, Basis &B);
+void footprint(const vr_camera &c, const Basis &B, const int box[6], double nmax, int rect[4]);
+
+}  // namespace host
+}  // namespace vr
+
+// Return the CUDA error of `call` as a vr_status with the context's message.
+#define VR_CUDA(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)

@@ -226,5 +226,59 @@ def quantize(vol: np.ndarray, storage: str) -> np.ndarray:
     return t.view(torch.int16).numpy().view(np.uint16)
 
 
+# --------------------------------------------------------------------------
+# Time-varying multi-field data (batching workload), generated with torch on a
+# chosen device because 18 x 768^3 volumes take minutes in numpy
+# --------------------------------------------------------------------------
+
+
+@dataclass(frozen=True)
+class FieldDraws:
+    blobs: Blobs
+    velocity: np.ndarray   # (n_blobs, 3) per-step displacement
+    lattice: np.ndarray    # (L+1)^3 noise lattice values U[0,1]
+
+
+def draw_fields(seed: int = 3, n_fields: int = 3, n_blobs: int = 8, cells: int = 16):
+    """Per field, draws in order: blobs (draw_blobs), n_blobs*3 velocities
+    U[-0.05, 0.05], a (cells+1)^3 noise lattice U[0,1]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_fields):
+        blobs = draw_blobs(rng, n_blobs)
+        vel = rng.uniform(-0.05, 0.05, size=(n_blobs, 3))
+        lat = rng.uniform(0.0, 1.0, size=(cells + 1,) * 3)
+        out.append(FieldDraws(blobs, vel, lat))
+    return out
+
+
+def field_volume_torch(draws: FieldDraws, step: int, n: int, device="cuda", noise_amp: float = 0.05):
+    """Field at time step `step`: the blobs moved by step * velocity, plus the
+    field's lattice noise (trilinear at voxel centres, lattice spacing
+    1/cells) times noise_amp. float32 [n, n, n] on `device`."""
+    import torch
+    x = (torch.arange(n, dtype=torch.float64, device=device) + 0.5) / n
+    out = torch.zeros((n, n, n), dtype=torch.float32, device=device)
+    for (cx, cy, cz), v, s_, a in zip(draws.blobs.centers, draws.velocity, draws.blobs.sigmas, draws.blobs.amps):
+        cx, cy, cz = cx + step * v[0], cy + step * v[1], cz + step * v[2]
+        gx = torch.exp(-((x - cx) ** 2) / (2 * s_ * s_))
+        gy = torch.exp(-((x - cy) ** 2) / (2 * s_ * s_))
+        gz = a * torch.exp(-((x - cz) ** 2) / (2 * s_ * s_))
+        out += (gz[:, None, None] * gy[None, :, None] * gx[None, None, :]).float()
+    cells = draws.lattice.shape[0] - 1
+    lat = torch.from_numpy(draws.lattice).to(device=device, dtype=torch.float32)
+    pos = x * cells
+    i0 = torch.clamp(torch.floor(pos).long(), max=cells - 1)
+    w = (pos - i0).float()
+    for axis in (2, 1, 0):
+        shape = [1, 1, 1]
+        shape[axis] = n
+        a0 = torch.index_select(lat, axis, i0)
+        a1 = torch.index_select(lat, axis, i0 + 1)
+        lat = a0 + w.reshape(shape) * (a1 - a0)
+    out += noise_amp * lat
+    return out
+
+
 def volume_range(vol: np.ndarray):
     return float(vol.min()), float(vol.max())

@@ -35,7 +35,8 @@ EXPORTS = (
     "vr_render_partials", "vr_frame_info", "vr_frame_partial", "vr_composite",
     "vr_frame_release", "vr_render_frame", "vr_partition_boxes", "vr_plan_view",
     "vr_set_kernel_timing", "vr_get_kernel_timing", "vr_render_frame_noalloc",
-    "vr_volume_update", "vr_render_backward",
+    "vr_volume_update", "vr_render_backward", "vr_batch_create", "vr_batch_launch",
+    "vr_batch_autotune", "vr_batch_release", "vr_batch_configure",
 )
 
 
@@ -88,6 +89,11 @@ _SIG = {
                                      ctypes.c_float, ctypes.POINTER(vr_camera), ctypes.c_float,
                                      ctypes.c_float, _P, _P]),
     "vr_volume_update": (_I, [_P, _P, _I, _P]),
+    "vr_batch_create": (_I, [_P, _I, _P, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
+    "vr_batch_launch": (_I, [_P, _P]),
+    "vr_batch_autotune": (_I, [_P, _P, ctypes.c_char_p, _P]),
+    "vr_batch_release": (_I, [_P]),
+    "vr_batch_configure": (_I, [_P, _I, _I, _I]),
     "vr_render_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
     "vr_plan_view": (_I, [_P, ctypes.POINTER(vr_partition), ctypes.POINTER(vr_camera), _P, _P]),
@@ -229,6 +235,45 @@ def vr_volume_create(ctx, volume, storage: str = "f32", partition=None, stream=N
     _check(lib().vr_volume_create(ctx, dims, DTYPES[storage], ctypes.byref(part), ptr, on_dev,
                                   _stream(stream), ctypes.byref(h)), ctx, "vr_volume_create")
     return h
+
+
+def vr_batch_create(ctx, vols, cams, out, vmins=None, vmaxs=None):
+    """Batch of len(vols) x len(cams) renders into `out` ([n_vols * n_views, H, W, 4]
+    CUDA float32; render r = v * n_views + w)."""
+    nv = len(vols)
+    vh = (ctypes.c_void_p * nv)(*[v.value for v in vols])
+    cs = (vr_camera * len(cams))(*[camera_struct(c) for c in cams])
+    lo = np.ascontiguousarray(vmins, dtype=np.float32) if vmins is not None else None
+    hi = np.ascontiguousarray(vmaxs, dtype=np.float32) if vmaxs is not None else None
+    optr, oon, _ = _ptr_and_loc(out)
+    if not oon:
+        raise ValueError("out must be a CUDA tensor")
+    h = ctypes.c_void_p()
+    _check(lib().vr_batch_create(ctx, nv, vh, lo.ctypes.data if lo is not None else None,
+                                 hi.ctypes.data if hi is not None else None, len(cams), cs, optr,
+                                 ctypes.byref(h)), ctx, "vr_batch_create")
+    return h
+
+
+def vr_batch_launch(batch, stream=None):
+    _check(lib().vr_batch_launch(batch, _stream(stream)), None, "vr_batch_launch")
+
+
+def vr_batch_autotune(batch, cache_path=None, stream=None):
+    """Returns (packet width, blocks per SM, ring slots, work order) of the fastest candidate."""
+    chosen = (ctypes.c_int * 4)()
+    _check(lib().vr_batch_autotune(batch, _stream(stream), cache_path.encode() if cache_path else None,
+                                   chosen), None, "vr_batch_autotune")
+    return tuple(chosen)
+
+
+def vr_batch_configure(batch, packet_width: int = 8, blocks_per_sm: int = 0, order: int = 0):
+    _check(lib().vr_batch_configure(batch, int(packet_width), int(blocks_per_sm), int(order)), None,
+           "vr_batch_configure")
+
+
+def vr_batch_release(batch):
+    _check(lib().vr_batch_release(batch), None, "vr_batch_release")
 
 
 def vr_volume_update(vol, volume, stream=None):
