@@ -51,6 +51,27 @@ def args_parse():
     return ap.parse_args()
 
 
+def shard_views(rank: int, world: int, n_views: int, n_frames: int):
+    """View index of each frame a rank renders: rank r takes views r, r+N,
+    r+2N, ... of the orbit (replicas of the volume over views, no data-path
+    exchange)."""
+    return [(rank + world * i) % n_views for i in range(n_frames)]
+
+
+def reduce_job(ms: float, e2e_s: float, samples: float, world: int, device: str = "cuda"):
+    """Whole-job numbers over ranks: the slowest rank's times, the sum of the
+    samples."""
+    if world <= 1:
+        return ms, e2e_s, samples
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    sm = torch.tensor([samples], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(sm[0])
+
+
 def recorded_traffic():
     """DRAM bytes per march launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
@@ -258,7 +279,7 @@ def run_ours(a):
         _, rects = vr.vr_plan_view(vol.shape[::-1], wl["part"], cam)
         rect_px.append(int(sum(int(r[2]) * int(r[3]) for r in rects)))
     vr.vr_set_count_samples(ctx, False)
-    views = [(rank + world * i) % len(cams) for i in range(a.warmup + a.steps)]
+    views = shard_views(rank, world, len(cams), a.warmup + a.steps)
 
     def barrier():
         if world > 1:
@@ -303,14 +324,7 @@ def run_ours(a):
     barrier()
 
     samples = float(sum(counts[vi] for vi in timed_views))
-    tensor = torch.tensor([ms, e2e_s, samples], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        mx = tensor[:2].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tensor[2:].clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms, e2e_s, samples = float(mx[0]), float(mx[1]), float(sm[0])
+    ms, e2e_s, samples = reduce_job(ms, e2e_s, samples, world)
     vr.vr_volume_release(v)
     vr.vr_destroy(ctx)
     if rank != 0:
