@@ -56,6 +56,7 @@ typedef struct {
     double ert_bias;        /* added to the termination threshold (ambiguity probes) */
     double end_bias;        /* added to t_out in the sample-count test (ambiguity probes) */
     const double *tf64;     /* optional: ntf x 4 table in double, used instead of tf */
+    int ert_global;         /* ray-state cycling: one (C, T) along the whole ray, global termination */
 } orc_scene;
 
 /* ---- scalar helpers ---------------------------------------------------- */
@@ -270,6 +271,8 @@ static long long render_pixel(const orc_scene *sc, int px, int py, pixel_ws *ws,
         const int ert = sc->ert_alpha < 1.0;
         const double thr = (1.0 - sc->ert_alpha) + sc->ert_bias;
         int cur = 0;
+        double gT = 1.0;
+        int gdone = 0;
         for (long long k = 0;; ++k) {
             double t = t_in + (k + 0.5) * dt;
             if (!(t < t_out + sc->end_bias)) break;
@@ -286,6 +289,20 @@ static long long render_pixel(const orc_scene *sc, int px, int py, pixel_ws *ws,
                 if (cur < 0) { cur = 0; ws->bad = 1; continue; } /* partition leaves a gap */
             }
             if (ws->first[cur] < 0) ws->first[cur] = k;
+            if (sc->ert_global) {
+                /* ray-state cycling (the paper's ray-queue cycling, Sec. 2.2 / 3,
+                 * restated for volumes): the ray carries one (C, T) through the
+                 * bricks in the order it meets them and stops everywhere once T
+                 * falls to the threshold */
+                if (gdone) break;
+                double rgba[4];
+                classify(sc, sample_trilinear(sc, p), rgba);
+                for (int ch = 0; ch < 3; ++ch) out[ch] += gT * rgba[3] * rgba[ch];
+                gT *= 1.0 - rgba[3];
+                ++executed;
+                if (ert && gT <= thr) gdone = 1;
+                continue;
+            }
             if (ws->done[cur]) continue;
             double rgba[4];
             classify(sc, sample_trilinear(sc, p), rgba);
@@ -295,7 +312,12 @@ static long long render_pixel(const orc_scene *sc, int px, int py, pixel_ws *ws,
             ++executed;
             if (ert && ws->T[cur] <= thr) ws->done[cur] = 1;
         }
+        if (sc->ert_global) {
+            out[3] = 1.0 - gT;
+            goto partials;
+        }
         /* front-to-back order along this ray = order of first owned sample */
+        {
         int m = 0;
         for (int b = 0; b < nb; ++b)
             if (ws->first[b] >= 0) {
@@ -312,7 +334,9 @@ static long long render_pixel(const orc_scene *sc, int px, int py, pixel_ws *ws,
             for (int ch = 0; ch < 3; ++ch) out[ch] += w * ws->C[3 * b + ch];
             out[3] += w * Ab;
         }
+        }
     }
+partials:
     if (partials_px)
         for (int b = 0; b < nb; ++b) {
             double *q = partials_px + b * pstride;

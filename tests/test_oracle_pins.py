@@ -380,3 +380,40 @@ def test_kd_partition_rules():
     for n in (5, 36, 64):
         dd = (96, 80, 72)
         _check_tiling(oracle.kd_partition(dd, n, rng.uniform(0.3, 0.7, n - 1)), dd)
+
+
+# --------------------------------------------------------------------------
+# Ray-state cycling (one (C, T) carried through the bricks, global termination)
+# --------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("split", ["grid", "kd"])
+def test_cycling_without_termination_equals_sort_last(split):
+    vol, tf, lo, hi = _scene()
+    n = 24
+    cam = synth.orbit_camera(18, 13, 250.0, elevation_deg=-15.0)
+    rng = np.random.default_rng(4)
+    boxes = (oracle.grid_partition((n,) * 3, (3, 2, 2)) if split == "grid"
+             else oracle.kd_partition((n,) * 3, 9, rng.uniform(0.3, 0.7, 8)))
+    a = oracle.render(vol, boxes, tf, lo, hi, cam, 0.5)
+    b = oracle.render(vol, boxes, tf, lo, hi, cam, 0.5, ert_global=True)
+    np.testing.assert_allclose(b["img"], a["img"], atol=1e-12)
+    assert a["nsamples"] == b["nsamples"]
+
+
+@pytest.mark.parametrize("alpha", [0.02, 0.05, 0.2])
+def test_cycling_global_termination_closed_form(alpha):
+    """Bricks stacked along z: the ray stops after the first sample anywhere
+    with T <= 0.01, k* = ceil(log 0.01 / log(1-alpha)) samples in all."""
+    n, gz = 64, 4
+    vol = np.full((n, n, n), 0.5, np.float32)
+    tf = synth.constant_tf([1.0, 0.5, 0.25, alpha])
+    alpha = float(tf[0, 3])
+    cam = synth.ortho_camera_z(4, 4)
+    boxes = oracle.grid_partition((n, n, n), (1, 1, gz))
+    out = oracle.render(vol, boxes, tf, 0.0, 1.0, cam, 0.5, ert_alpha=0.99, ert_global=True)
+    taken = min(2 * n, math.ceil(math.log(0.01) / math.log(1 - alpha)))
+    np.testing.assert_allclose(out["img"][..., 3], 1 - (1 - alpha) ** taken, atol=1e-12)
+    assert out["nsamples"] == 16 * taken
+    local = oracle.render(vol, boxes, tf, 0.0, 1.0, cam, 0.5, ert_alpha=0.99)
+    assert local["nsamples"] >= out["nsamples"]
