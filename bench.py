@@ -325,6 +325,35 @@ def run_ours(a):
 
     samples = float(sum(counts[vi] for vi in timed_views))
     ms, e2e_s, samples = reduce_job(ms, e2e_s, samples, world)
+
+    # ray-state cycling on the same frames (rays carry (C, T) through the bricks,
+    # global early termination): executed samples and frame time
+    cyc = None
+    if world == 1:
+        vr.vr_set_render_mode(ctx, 1)
+        vr.vr_set_count_samples(ctx, True)
+        ccounts = []
+        for cam in cams:
+            vr.vr_set_camera(ctx, cam)
+            vr.vr_render_frame(ctx, v, out)
+            ccounts.append(vr.vr_get_sample_count(ctx))
+        vr.vr_set_count_samples(ctx, False)
+        for i in range(a.warmup):
+            vr.vr_set_camera(ctx, cams[views[i]])
+            vr.vr_render_frame(ctx, v, out)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for vi in timed_views:
+            vr.vr_set_camera(ctx, cams[vi])
+            vr.vr_render_frame(ctx, v, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1)
+        csamp = float(sum(ccounts[vi] for vi in timed_views))
+        cyc = dict(ms_per_frame=cms / len(timed_views), frames_per_s=len(timed_views) / (cms / 1e3),
+                   samples_per_s=csamp / (cms / 1e3), samples_per_frame=csamp / len(timed_views),
+                   speedup_vs_sort_last=ms / cms)
+        vr.vr_set_render_mode(ctx, 0)
     vr.vr_volume_release(v)
     vr.vr_destroy(ctx)
     if rank != 0:
@@ -382,6 +411,7 @@ def run_ours(a):
                           composite=dict(achieved=comp_gbs, peak=hbm, unit="GB/s", frac=comp_gbs / hbm,
                                          note="partial reads + image write / composite time, %s" % hbm_src)),
         kernel_ms=dict(march=march_ms, composite=comp_ms),
+        ray_state_cycling=cyc,
         cpu_baseline=cpu,
         e2e=dict(value=samples / e2e_s, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=W * H * 16,
                  note="vr_render_frame into pinned host memory: render + 33 MB device-to-host copy + wait "

@@ -168,6 +168,18 @@ vr_status vr_set_render_params(vr_ctx ctx, float step_voxels, float ert_alpha);
  * visibility order are combined first, then groups of factors[1] of those, ...).
  * n_factors == 0 selects direct k-way compositing. At most 8 factors. */
 vr_status vr_set_composite_schedule(vr_ctx ctx, int n_factors, const int *factors);
+/* Frame algorithm of vr_render_frame.
+ *   0 (default): sort-last -- one partial image per brick, then the "over"
+ *     composite (the steps above).
+ *   1: ray-state cycling -- each ray carries one (C, T) through the bricks in
+ *     front-to-back order and writes its pixel directly (the paper's ray-queue
+ *     cycling, where every ray visits every rank, Sec. 2.2 and 3, restated for
+ *     bricks on one GPU). No partial images; early termination applies to the
+ *     whole ray (T <= 1 - ert_alpha), not per brick. With early termination off
+ *     it computes the same image as mode 0 up to rounding.
+ * vr_render_partials, vr_composite and vr_render_backward always use the
+ * sort-last steps. */
+vr_status vr_set_render_mode(vr_ctx ctx, int mode);
 /* When on, every march launch also counts executed samples (see
  * vr_get_sample_count). Off by default. */
 vr_status vr_set_count_samples(vr_ctx ctx, int on);

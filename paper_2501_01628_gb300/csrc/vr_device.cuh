@@ -169,15 +169,16 @@ __device__ __forceinline__ void owned_run(const P &p, const BrickLaunch &B, int 
 }
 
 // Front-to-back emission-absorption over one owned run (see include/vr.h):
-// C += T alpha rgb, T *= (1 - alpha), with the two samples of an iteration
-// requesting their cells' quads before either is classified, and a sample in
-// the previous sample's cell reusing its quads. Returns the partial (C, 1 - T).
+// C += T alpha rgb, T *= (1 - alpha), continuing from the state (C, T) passed
+// in, and stopping once T <= ert_T. The two samples of an iteration request
+// their cells' quads before either is classified, and a sample in the previous
+// sample's cell reuses its quads.
 template <typename S, bool COUNT>
-__device__ __forceinline__ float4 march_run(const void *data, const BrickLaunch &B, const OwnedRun &run,
-                                            const float4 *tf, float tf_scale, float tf_bias, int ntf, float ert_T,
-                                            unsigned long long &executed)
+__device__ __forceinline__ void march_accumulate(const void *data, const BrickLaunch &B, const OwnedRun &run,
+                                                 const float4 *tf, float tf_scale, float tf_bias, int ntf,
+                                                 float ert_T, float &C0, float &C1, float &C2, float &T,
+                                                 unsigned long long &executed)
 {
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
     {
         const int ka = run.ka, kb = run.kb;
         // owned samples are contiguous along the ray: [ka, kb] are all owned
@@ -253,6 +254,16 @@ __device__ __forceinline__ float4 march_run(const void *data, const BrickLaunch 
             }
         }
     }
+}
+
+// One brick's partial from a fresh state: (C, 1 - T).
+template <typename S, bool COUNT>
+__device__ __forceinline__ float4 march_run(const void *data, const BrickLaunch &B, const OwnedRun &run,
+                                            const float4 *tf, float tf_scale, float tf_bias, int ntf, float ert_T,
+                                            unsigned long long &executed)
+{
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+    march_accumulate<S, COUNT>(data, B, run, tf, tf_scale, tf_bias, ntf, ert_T, C0, C1, C2, T, executed);
     return make_float4(C0, C1, C2, 1.0f - T);
 }
 

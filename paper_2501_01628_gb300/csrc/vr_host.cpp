@@ -425,6 +425,7 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
     mp.sample_counter = ctx->count_samples ? ctx->d_counter : nullptr;
     mp.nb = nb;
     mp.n_items = items;
+    for (int j = 0; j < nb; ++j) mp.order[j] = fr.order[j];
     return VR_OK;
 }
 
@@ -528,6 +529,35 @@ vr_status composite_to(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device
     VR_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_img, static_cast<size_t>(px) * sizeof(float4),
                                  cudaMemcpyDeviceToHost, s));
     VR_CUDA(ctx, cudaStreamSynchronize(s));
+    return VR_OK;
+}
+
+// Ray-state cycling frame straight into the image (device or host output).
+vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cudaStream_t s)
+{
+    if (!out) return fail(ctx, VR_ERR_ARG, "null output");
+    static thread_local MarchParams mp;
+    vr_status st = prepare_frame(ctx, vol, ctx->frame, mp);
+    if (st != VR_OK) return st;
+    const long long px = static_cast<long long>(mp.W) * mp.H;
+    float4 *dst = reinterpret_cast<float4 *>(out);
+    if (!out_on_device) {
+        if (px > ctx->img_cap) {
+            if (ctx->d_img) cudaFree(ctx->d_img);
+            ctx->d_img = nullptr;
+            ctx->img_cap = 0;
+            VR_CUDA(ctx, cudaMalloc(&ctx->d_img, static_cast<size_t>(px) * sizeof(float4)));
+            ctx->img_cap = px;
+        }
+        dst = ctx->d_img;
+    }
+    const int t = timing_begin(ctx, 0, s);
+    VR_CUDA(ctx, launch_march_cycle(mp, vol->dtype, dst, s));
+    timing_end(ctx, t, s);
+    if (!out_on_device) {
+        VR_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_img, static_cast<size_t>(px) * sizeof(float4), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(ctx, cudaStreamSynchronize(s));
+    }
     return VR_OK;
 }
 
@@ -1005,9 +1035,18 @@ vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on
     if (vol->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume belongs to another context");
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ctx->mode == 1) return cycle_to(ctx, vol, out_rgba, out_on_device, s);
     vr_status st = march(ctx, vol, ctx->frame, s);
     if (st != VR_OK) return st;
     return composite_to(ctx, ctx->frame, out_rgba, out_on_device, s);
+}
+
+vr_status vr_set_render_mode(vr_ctx ctx, int mode)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (mode != 0 && mode != 1) return fail(ctx, VR_ERR_ARG, "render mode must be 0 or 1");
+    ctx->mode = mode;
+    return VR_OK;
 }
 
 }  // extern "C"

@@ -64,6 +64,7 @@ struct MarchParams {
     unsigned long long *sample_counter;  // non-null: count executed samples
     int nb;
     int n_items;
+    int order[kMaxBricks];  // brick ids front to back (ray-state cycling)
     BrickLaunch b[kMaxBricks];
 };
 
@@ -162,6 +163,7 @@ struct PackParams {
 // Launchers (vr_kernels.cu). They return the launch's cudaError_t.
 cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s);
 cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s);
+cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out, cudaStream_t s);
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s);
 cudaError_t launch_composite_grad(const CompositeGradParams &p, cudaStream_t s);
 cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, vr_dtype dtype, cudaStream_t s);

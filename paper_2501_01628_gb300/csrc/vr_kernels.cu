@@ -74,6 +74,35 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
 }
 
 // ---------------------------------------------------------------------------
+// Ray-state cycling: one thread per image pixel carries (C, T) through the
+// bricks in front-to-back order (the paper's ray-queue cycling, Sec. 2.2 and 3,
+// where every ray visits every rank, restated for bricks on one GPU). No
+// partial images and no composite; early termination is global.
+// ---------------------------------------------------------------------------
+template <typename S, bool COUNT>
+__global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant__ MarchParams p, float4 *out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    if (px >= p.W || py >= p.H) return;
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+    unsigned long long executed = 0;
+    for (int j = 0; j < p.nb; ++j) {
+        const BrickLaunch &B = p.b[p.order[j]];
+        if (px < B.rect[0] || px >= B.rect[0] + B.rect[2] || py < B.rect[1] || py >= B.rect[1] + B.rect[3])
+            continue;
+        dev::OwnedRun run;
+        dev::owned_run(p, B, px, py, run);
+        dev::march_accumulate<S, COUNT>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, C0, C1, C2, T,
+                                        executed);
+        if (T <= p.ert_T) break;
+    }
+    out[static_cast<long long>(py) * p.W + px] = make_float4(C0, C1, C2, 1.0f - T);
+    if (COUNT && executed) atomicAdd(p.sample_counter, executed);
+}
+
+// ---------------------------------------------------------------------------
 // Composite: one block per 32x8 image tile, one thread per pixel; partials are
 // combined front to back with "over" along the configured association tree.
 // ---------------------------------------------------------------------------
@@ -204,6 +233,24 @@ cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s)
     default: return cudaErrorInvalidValue;
     }
 #undef VR_MARCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out, cudaStream_t s)
+{
+    if (p.W <= 0 || p.H <= 0) return cudaSuccess;
+    const dim3 grid((p.W + kTileW - 1) / kTileW, (p.H + kTileH - 1) / kTileH);
+    const bool count = p.sample_counter != nullptr;
+#define VR_CYCLE(T)                                                                   \
+    (count ? (march_cycle_kernel<T, true><<<grid, 128, 0, s>>>(p, out), 0)            \
+           : (march_cycle_kernel<T, false><<<grid, 128, 0, s>>>(p, out), 0))
+    switch (dtype) {
+    case VR_F32: VR_CYCLE(float); break;
+    case VR_BF16: VR_CYCLE(__nv_bfloat16); break;
+    case VR_F16: VR_CYCLE(__half); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef VR_CYCLE
     return cudaGetLastError();
 }
 

@@ -60,6 +60,7 @@ struct vr_ctx_s {
     float step = 0.5f;
     float ert_alpha = 1.0f;
     std::vector<int> factors;
+    int mode = 0;                  // 0: sort-last partials + composite; 1: ray-state cycling
     unsigned long long *d_counter = nullptr;
     int *d_error = nullptr;        // device error word (vr_sync reports and clears it)
     bool count_samples = false;
