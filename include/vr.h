@@ -168,6 +168,13 @@ vr_status vr_set_render_params(vr_ctx ctx, float step_voxels, float ert_alpha);
  * visibility order are combined first, then groups of factors[1] of those, ...).
  * n_factors == 0 selects direct k-way compositing. At most 8 factors. */
 vr_status vr_set_composite_schedule(vr_ctx ctx, int n_factors, const int *factors);
+/* Opacity correction (off by default): with ref_step_voxels > 0, each sample's
+ * table opacity alpha is replaced by 1 - (1 - alpha)^(step_voxels /
+ * ref_step_voxels), so the table means "opacity per ref_step_voxels of path" and
+ * the image no longer depends on the step (the paper fixes no optical model;
+ * this is the standard correction of emission-absorption ray casting).
+ * ref_step_voxels == 0 turns it off. Not available in vr_render_backward. */
+vr_status vr_set_opacity_correction(vr_ctx ctx, float ref_step_voxels);
 /* Frame algorithm of vr_render_frame.
  *   0 (default): sort-last -- one partial image per brick, then the "over"
  *     composite (the steps above).

@@ -61,7 +61,8 @@ class _Scene(ctypes.Structure):
                 ("vmax", ctypes.c_double), ("cam", _Camera),
                 ("step_voxels", ctypes.c_double), ("ert_alpha", ctypes.c_double),
                 ("ert_bias", ctypes.c_double), ("end_bias", ctypes.c_double),
-                ("tf64", ctypes.c_void_p), ("ert_global", ctypes.c_int)]
+                ("tf64", ctypes.c_void_p), ("ert_global", ctypes.c_int),
+                ("opc_ratio", ctypes.c_double)]
 
 
 def lib():
@@ -200,7 +201,8 @@ def primary_ray(cam, px, py):
 def render(vol: np.ndarray, boxes, tf: np.ndarray, vmin: float, vmax: float, cam: dict,
            step_voxels: float = 0.5, ert_alpha: float = 1.0, pixels=None, crop=None,
            dtype=None, with_partials: bool = False, ert_bias: float = 0.0,
-           end_bias: float = 0.0, threads: int | None = None, ert_global: bool = False):
+           end_bias: float = 0.0, threads: int | None = None, ert_global: bool = False,
+           opacity_ref_step: float = 0.0):
     """Render pixels with the FP64 oracle.
 
     vol     [Nz, Ny, Nx] array (float32/float64, or uint16 bits with dtype BF16/F16)
@@ -213,6 +215,7 @@ def render(vol: np.ndarray, boxes, tf: np.ndarray, vmin: float, vmax: float, cam
     sc.ert_bias = float(ert_bias)
     sc.end_bias = float(end_bias)
     sc.ert_global = int(bool(ert_global))
+    sc.opc_ratio = float(step_voxels) / opacity_ref_step if opacity_ref_step > 0 else 0.0
     W, H = int(cam["width"]), int(cam["height"])
     shape = None
     if pixels is None:

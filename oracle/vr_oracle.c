@@ -57,6 +57,7 @@ typedef struct {
     double end_bias;        /* added to t_out in the sample-count test (ambiguity probes) */
     const double *tf64;     /* optional: ntf x 4 table in double, used instead of tf */
     int ert_global;         /* ray-state cycling: one (C, T) along the whole ray, global termination */
+    double opc_ratio;       /* opacity correction step/reference step; 0 or 1 = off */
 } orc_scene;
 
 /* ---- scalar helpers ---------------------------------------------------- */
@@ -151,6 +152,10 @@ static void classify(const orc_scene *sc, double s, double rgba[4])
     double w = x - i;
     for (int c = 0; c < 4; ++c)
         rgba[c] = (1.0 - w) * tf_entry(sc, i, c) + w * tf_entry(sc, i + 1, c);
+    /* opacity correction (reading; not in the paper): the table holds the
+     * opacity of a reference step; a step r times as long keeps the same
+     * transmittance per path length: alpha' = 1 - (1 - alpha)^r */
+    if (sc->opc_ratio > 0.0 && sc->opc_ratio != 1.0) rgba[3] = 1.0 - pow(1.0 - rgba[3], sc->opc_ratio);
 }
 
 /* ---- primary rays (Sec. 2.1: rays originate at the virtual camera) -----
@@ -509,7 +514,7 @@ int orc_render_grad(const orc_scene *sc, int m, const int *pix, const double *gr
                     double *grad_vol, int nthreads)
 {
     if (!sc || sc->nb < 1 || sc->ntf < 2 || !(sc->vmax > sc->vmin) || sc->step_voxels <= 0 ||
-        sc->ert_alpha < 1.0)
+        sc->ert_alpha < 1.0 || (sc->opc_ratio > 0.0 && sc->opc_ratio != 1.0))
         return -2;
     const int nm = nmax3(sc->dims);
     const double E[3] = {(double)sc->dims[0] / nm, (double)sc->dims[1] / nm, (double)sc->dims[2] / nm};

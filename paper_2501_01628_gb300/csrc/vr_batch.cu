@@ -43,7 +43,7 @@ __device__ __forceinline__ bool wait_at_least(const int *addr, int target, int l
     return false;
 }
 
-template <typename S>
+template <typename S, bool OPC>
 __global__ void __launch_bounds__(128, 10) batch_kernel(const __grid_constant__ BatchParams p)
 {
     __shared__ long long s_item;
@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(128, 10) batch_kernel(const __grid_constant__ 
                 unsigned long long unused = 0;
                 const float2 sb = p.vol_tf[v];
                 part[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] =
-                    dev::march_run<S, false>(p.vol_data[v], B, run, p.tf, sb.x, sb.y, p.ntf, p.ert_T, unused);
+                    dev::march_run<S, false, OPC>(p.vol_data[v], B, run, p.tf, sb.x, sb.y, p.ntf, p.ert_T, unused,
+                                                  p.opc_ratio);
             }
             __threadfence();  // every writer publishes its partial before the count moves
             __syncthreads();
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(128, 10) batch_kernel(const __grid_constant__ 
     }
 }
 
-template <typename S>
+template <typename S, bool OPC>
 cudaError_t launch_batch_t(const BatchParams &p, int blocks, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
@@ -202,17 +203,19 @@ cudaError_t launch_batch_t(const BatchParams &p, int blocks, cudaStream_t s)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_kernel<S>, p);
+    return cudaLaunchKernelEx(&cfg, batch_kernel<S, OPC>, p);
 }
 
 }  // namespace
 
 cudaError_t launch_batch(const BatchParams &p, vr_dtype dtype, int blocks, cudaStream_t s)
 {
+    const bool opc = p.opc_ratio != 1.0f;
     switch (dtype) {
-    case VR_F32: return launch_batch_t<float>(p, blocks, s);
-    case VR_BF16: return launch_batch_t<__nv_bfloat16>(p, blocks, s);
-    case VR_F16: return launch_batch_t<__half>(p, blocks, s);
+    case VR_F32: return opc ? launch_batch_t<float, true>(p, blocks, s) : launch_batch_t<float, false>(p, blocks, s);
+    case VR_BF16:
+        return opc ? launch_batch_t<__nv_bfloat16, true>(p, blocks, s) : launch_batch_t<__nv_bfloat16, false>(p, blocks, s);
+    case VR_F16: return opc ? launch_batch_t<__half, true>(p, blocks, s) : launch_batch_t<__half, false>(p, blocks, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -222,9 +225,9 @@ int batch_max_blocks_per_sm(vr_dtype dtype)
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (dtype) {
-    case VR_F32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<float>, 128, 0); break;
-    case VR_BF16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<__nv_bfloat16>, 128, 0); break;
-    case VR_F16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<__half>, 128, 0); break;
+    case VR_F32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<float, true>, 128, 0); break;
+    case VR_BF16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<__nv_bfloat16, true>, 128, 0); break;
+    case VR_F16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<__half, true>, 128, 0); break;
     default: break;
     }
     return e == cudaSuccess ? n : 0;
@@ -447,6 +450,7 @@ vr_status build(vr_batch b, int pw, int bps, int mode)
     p.tf = ctx->d_tf;
     p.ntf = ctx->ntf;
     p.ert_T = ctx->ert_alpha < 1.0f ? static_cast<float>(1.0 - static_cast<double>(ctx->ert_alpha)) : -1.0f;
+    p.opc_ratio = ctx->opc_ref > 0.0f ? static_cast<float>(static_cast<double>(ctx->step) / ctx->opc_ref) : 1.0f;
     p.ring = b->d_ring;
     p.slot_px = unit_px;
     p.slots = slots;

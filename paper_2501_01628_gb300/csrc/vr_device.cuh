@@ -173,11 +173,13 @@ __device__ __forceinline__ void owned_run(const P &p, const BrickLaunch &B, int 
 // in, and stopping once T <= ert_T. The two samples of an iteration request
 // their cells' quads before either is classified, and a sample in the previous
 // sample's cell reuses its quads.
-template <typename S, bool COUNT>
+// OPC: opacity correction for a step other than the reference step,
+// alpha' = 1 - (1 - alpha)^ratio, evaluated as -expm1(ratio * log1p(-alpha)).
+template <typename S, bool COUNT, bool OPC = false>
 __device__ __forceinline__ void march_accumulate(const void *data, const BrickLaunch &B, const OwnedRun &run,
                                                  const float4 *tf, float tf_scale, float tf_bias, int ntf,
                                                  float ert_T, float &C0, float &C1, float &C2, float &T,
-                                                 unsigned long long &executed)
+                                                 unsigned long long &executed, float opc_ratio = 1.0f)
 {
     {
         const int ka = run.ka, kb = run.kb;
@@ -220,7 +222,9 @@ __device__ __forceinline__ void march_accumulate(const void *data, const BrickLa
                 const float w = x - static_cast<float>(ti);
                 const float4 e0 = __ldg(tf + 2 * ti), de = __ldg(tf + 2 * ti + 1);
                 const float r = fmaf(w, de.x, e0.x), g = fmaf(w, de.y, e0.y);
-                const float bb = fmaf(w, de.z, e0.z), al = fmaf(w, de.w, e0.w);
+                const float bb = fmaf(w, de.z, e0.z);
+                float al = fmaf(w, de.w, e0.w);
+                if (OPC) al = -expm1f(opc_ratio * log1pf(-al));
                 const float ta = T * al;
                 C0 = fmaf(ta, r, C0);
                 C1 = fmaf(ta, g, C1);
@@ -257,13 +261,14 @@ __device__ __forceinline__ void march_accumulate(const void *data, const BrickLa
 }
 
 // One brick's partial from a fresh state: (C, 1 - T).
-template <typename S, bool COUNT>
+template <typename S, bool COUNT, bool OPC = false>
 __device__ __forceinline__ float4 march_run(const void *data, const BrickLaunch &B, const OwnedRun &run,
                                             const float4 *tf, float tf_scale, float tf_bias, int ntf, float ert_T,
-                                            unsigned long long &executed)
+                                            unsigned long long &executed, float opc_ratio = 1.0f)
 {
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
-    march_accumulate<S, COUNT>(data, B, run, tf, tf_scale, tf_bias, ntf, ert_T, C0, C1, C2, T, executed);
+    march_accumulate<S, COUNT, OPC>(data, B, run, tf, tf_scale, tf_bias, ntf, ert_T, C0, C1, C2, T, executed,
+                                    opc_ratio);
     return make_float4(C0, C1, C2, 1.0f - T);
 }
 

@@ -414,6 +414,7 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
     mp.dt = static_cast<float>(dt);
     mp.inv_dt = static_cast<float>(1.0 / dt);
     mp.ert_T = ctx->ert_alpha < 1.0f ? static_cast<float>(1.0 - static_cast<double>(ctx->ert_alpha)) : -1.0f;
+    mp.opc_ratio = ctx->opc_ref > 0.0f ? static_cast<float>(static_cast<double>(ctx->step) / ctx->opc_ref) : 1.0f;
     {
         const double scale = (ctx->ntf - 1) / (static_cast<double>(ctx->vmax) - ctx->vmin);
         mp.tf_scale = static_cast<float>(scale);
@@ -801,6 +802,7 @@ vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_d
     if (!grad_rgba_dev || !grad_tf_dev) return fail(ctx, VR_ERR_ARG, "null gradient buffer");
     if (vol->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume belongs to another context");
     if (ctx->ert_alpha < 1.0f) return fail(ctx, VR_ERR_ARG, "backward requires early termination off");
+    if (ctx->opc_ref > 0.0f) return fail(ctx, VR_ERR_ARG, "backward requires opacity correction off");
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     static thread_local MarchParams mp;
@@ -1039,6 +1041,15 @@ vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on
     vr_status st = march(ctx, vol, ctx->frame, s);
     if (st != VR_OK) return st;
     return composite_to(ctx, ctx->frame, out_rgba, out_on_device, s);
+}
+
+vr_status vr_set_opacity_correction(vr_ctx ctx, float ref_step_voxels)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (!(ref_step_voxels >= 0.0f) || !std::isfinite(ref_step_voxels))
+        return fail(ctx, VR_ERR_ARG, "bad reference step");
+    ctx->opc_ref = ref_step_voxels;
+    return VR_OK;
 }
 
 vr_status vr_set_render_mode(vr_ctx ctx, int mode)

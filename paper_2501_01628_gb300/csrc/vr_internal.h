@@ -55,6 +55,7 @@ struct MarchParams {
     float N[3];         // volume extent in voxels
     float dt, inv_dt;   // sample spacing (world units) and its inverse
     float ert_T;        // terminate a brick when T <= ert_T (negative: never)
+    float opc_ratio;    // opacity correction step / reference step (1: off)
     // classification
     float tf_scale, tf_bias;  // x = s*scale + bias = (s - vmin)/(vmax - vmin)*(ntf-1)
     int ntf;
@@ -141,6 +142,7 @@ struct BatchParams {
     const float4 *tf;                // (T, dT) pairs
     int ntf;
     float ert_T;
+    float opc_ratio;                 // opacity correction (1: off)
     float4 *ring;                    // slots x slot_px partial pixels
     long long slot_px;               // partial pixels per ring slot (one unit)
     int slots;

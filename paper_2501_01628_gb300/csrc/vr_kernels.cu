@@ -47,7 +47,7 @@ __global__ void pack_kernel(PackParams p)
 // ---------------------------------------------------------------------------
 // March: one thread per pixel of a brick's footprint; 8x4-pixel warp packets.
 // ---------------------------------------------------------------------------
-template <typename S, bool COUNT>
+template <typename S, bool COUNT, bool OPC>
 __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ MarchParams p)
 {
     // transfer function as (T[i], T[i+1]-T[i]) pairs; the last difference is 0
@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     unsigned long long executed = 0;
     dev::OwnedRun run;
     dev::owned_run(p, B, px, py, run);
-    const float4 c = dev::march_run<S, COUNT>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, executed);
+    const float4 c =
+        dev::march_run<S, COUNT, OPC>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, executed, p.opc_ratio);
     p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = c;
     if (COUNT && executed) atomicAdd(p.sample_counter, executed);
 }
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
 // where every ray visits every rank, restated for bricks on one GPU). No
 // partial images and no composite; early termination is global.
 // ---------------------------------------------------------------------------
-template <typename S, bool COUNT>
+template <typename S, bool COUNT, bool OPC>
 __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant__ MarchParams p, float4 *out)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -94,8 +95,8 @@ __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant_
             continue;
         dev::OwnedRun run;
         dev::owned_run(p, B, px, py, run);
-        dev::march_accumulate<S, COUNT>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, C0, C1, C2, T,
-                                        executed);
+        dev::march_accumulate<S, COUNT, OPC>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, C0, C1,
+                                             C2, T, executed, p.opc_ratio);
         if (T <= p.ert_T) break;
     }
     out[static_cast<long long>(py) * p.W + px] = make_float4(C0, C1, C2, 1.0f - T);
@@ -223,9 +224,12 @@ cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s)
 {
     if (p.n_items <= 0) return cudaSuccess;
     const bool count = p.sample_counter != nullptr;
-#define VR_MARCH(T)                                                                      \
-    (count ? (march_kernel<T, true><<<p.n_items, 128, 0, s>>>(p), 0)                     \
-           : (march_kernel<T, false><<<p.n_items, 128, 0, s>>>(p), 0))
+    const bool opc = p.opc_ratio != 1.0f;
+#define VR_MARCH(T)                                                                                     \
+    (opc ? (count ? (march_kernel<T, true, true><<<p.n_items, 128, 0, s>>>(p), 0)                       \
+                  : (march_kernel<T, false, true><<<p.n_items, 128, 0, s>>>(p), 0))                     \
+         : (count ? (march_kernel<T, true, false><<<p.n_items, 128, 0, s>>>(p), 0)                      \
+                  : (march_kernel<T, false, false><<<p.n_items, 128, 0, s>>>(p), 0)))
     switch (dtype) {
     case VR_F32: VR_MARCH(float); break;
     case VR_BF16: VR_MARCH(__nv_bfloat16); break;
@@ -241,9 +245,12 @@ cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out
     if (p.W <= 0 || p.H <= 0) return cudaSuccess;
     const dim3 grid((p.W + kTileW - 1) / kTileW, (p.H + kTileH - 1) / kTileH);
     const bool count = p.sample_counter != nullptr;
-#define VR_CYCLE(T)                                                                   \
-    (count ? (march_cycle_kernel<T, true><<<grid, 128, 0, s>>>(p, out), 0)            \
-           : (march_cycle_kernel<T, false><<<grid, 128, 0, s>>>(p, out), 0))
+    const bool opc = p.opc_ratio != 1.0f;
+#define VR_CYCLE(T)                                                                                    \
+    (opc ? (count ? (march_cycle_kernel<T, true, true><<<grid, 128, 0, s>>>(p, out), 0)                \
+                  : (march_cycle_kernel<T, false, true><<<grid, 128, 0, s>>>(p, out), 0))              \
+         : (count ? (march_cycle_kernel<T, true, false><<<grid, 128, 0, s>>>(p, out), 0)               \
+                  : (march_cycle_kernel<T, false, false><<<grid, 128, 0, s>>>(p, out), 0)))
     switch (dtype) {
     case VR_F32: VR_CYCLE(float); break;
     case VR_BF16: VR_CYCLE(__nv_bfloat16); break;

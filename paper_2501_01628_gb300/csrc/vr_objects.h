@@ -61,6 +61,7 @@ struct vr_ctx_s {
     float ert_alpha = 1.0f;
     std::vector<int> factors;
     int mode = 0;                  // 0: sort-last partials + composite; 1: ray-state cycling
+    float opc_ref = 0.0f;          // opacity-correction reference step in voxels (0: off)
     unsigned long long *d_counter = nullptr;
     int *d_error = nullptr;        // device error word (vr_sync reports and clears it)
     bool count_samples = false;

@@ -37,6 +37,7 @@ EXPORTS = (
     "vr_set_kernel_timing", "vr_get_kernel_timing", "vr_render_frame_noalloc",
     "vr_volume_update", "vr_render_backward", "vr_batch_create", "vr_batch_launch",
     "vr_batch_autotune", "vr_batch_release", "vr_batch_configure", "vr_set_render_mode",
+    "vr_set_opacity_correction",
 )
 
 
@@ -95,6 +96,7 @@ _SIG = {
     "vr_batch_release": (_I, [_P]),
     "vr_batch_configure": (_I, [_P, _I, _I, _I]),
     "vr_set_render_mode": (_I, [_P, _I]),
+    "vr_set_opacity_correction": (_I, [_P, ctypes.c_float]),
     "vr_render_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
     "vr_plan_view": (_I, [_P, ctypes.POINTER(vr_partition), ctypes.POINTER(vr_camera), _P, _P]),
@@ -356,6 +358,11 @@ def vr_set_composite_schedule(ctx, factors=()):
     f = np.ascontiguousarray(list(factors), dtype=np.int32)
     _check(lib().vr_set_composite_schedule(ctx, int(f.size), f.ctypes.data if f.size else None),
            ctx, "vr_set_composite_schedule")
+
+
+def vr_set_opacity_correction(ctx, ref_step_voxels: float):
+    """alpha' = 1 - (1 - alpha)^(step / ref_step) per sample; 0 turns it off."""
+    _check(lib().vr_set_opacity_correction(ctx, float(ref_step_voxels)), ctx, "vr_set_opacity_correction")
 
 
 def vr_set_render_mode(ctx, mode: int):

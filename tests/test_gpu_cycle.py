@@ -100,3 +100,34 @@ def test_cycling_paper_workload_sampled(vr):
     pix = np.stack([prng.integers(0, 1920, 2048), prng.integers(0, 1080, 2048)], axis=1)
     env = oracle_env(vol, boxes, tf, lo, hi, cam, 0.5, 0.99, ert_global=True, pixels=pix)
     compare_envelope(got[pix[:, 1], pix[:, 0]], env)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("step", [0.25, 0.8])
+def test_opacity_correction(vr, mode, step):
+    import torch
+    n = 40
+    rng = np.random.default_rng(900)
+    vol = synth.blob_volume(n, synth.draw_blobs(rng, 6))
+    tf = synth.random_tf(rng, alpha_max=0.2)
+    lo, hi = synth.volume_range(vol)
+    part = dict(kind="kd", n_bricks=5, cut_fracs=[0.4, 0.6, 0.45, 0.55])
+    cam = synth.orbit_camera(56, 48, 120.0)
+    ctx = vr.vr_create(0)
+    v = vr.vr_volume_create(ctx, vol, "f32", part)
+    try:
+        vr.vr_set_transfer_function(ctx, tf, lo, hi)
+        vr.vr_set_camera(ctx, cam)
+        vr.vr_set_render_params(ctx, step, 1.0)
+        vr.vr_set_opacity_correction(ctx, 0.5)
+        vr.vr_set_render_mode(ctx, mode)
+        out = torch.empty((48, 56, 4), device="cuda")
+        vr.vr_render_frame(ctx, v, out)
+        vr.vr_sync(ctx)
+        got = out.cpu().numpy().astype(np.float64)
+    finally:
+        vr.vr_volume_release(v)
+        vr.vr_destroy(ctx)
+    boxes = vr.vr_partition_boxes((n,) * 3, part)
+    compare_envelope(got, oracle_env(vol, boxes, tf, lo, hi, cam, step, opacity_ref_step=0.5,
+                                     ert_global=(mode == 1)))

@@ -417,3 +417,32 @@ def test_cycling_global_termination_closed_form(alpha):
     assert out["nsamples"] == 16 * taken
     local = oracle.render(vol, boxes, tf, 0.0, 1.0, cam, 0.5, ert_alpha=0.99)
     assert local["nsamples"] >= out["nsamples"]
+
+
+# --------------------------------------------------------------------------
+# Opacity correction: alpha' = 1 - (1 - alpha)^(step / reference step)
+# --------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("alpha", [0.01, 0.05, 0.3])
+@pytest.mark.parametrize("step", [0.25, 0.5, 1.0])
+def test_opacity_correction_makes_the_slab_step_invariant(alpha, step):
+    n = 32
+    vol = np.full((n, n, n), 0.5, np.float32)
+    tf = synth.constant_tf([0.8, 0.6, 0.4, alpha])
+    alpha = float(tf[0, 3])
+    cam = synth.ortho_camera_z(4, 4)
+    boxes = oracle.grid_partition((n, n, n), (1, 1, 2))
+    out = oracle.render(vol, boxes, tf, 0.0, 1.0, cam, step, opacity_ref_step=0.5)
+    # the chord is n voxels; the reference step 0.5 gives 2n samples of alpha
+    np.testing.assert_allclose(out["img"][..., 3], 1 - (1 - alpha) ** (2 * n), atol=1e-12)
+    np.testing.assert_allclose(out["img"][..., 0], 0.8 * (1 - (1 - alpha) ** (2 * n)), atol=1e-12)
+
+
+def test_opacity_correction_at_the_reference_step_is_the_identity():
+    vol, tf, lo, hi = _scene()
+    cam = synth.orbit_camera(10, 9, 30.0)
+    boxes = oracle.grid_partition((24,) * 3, (2, 2, 2))
+    a = oracle.render(vol, boxes, tf, lo, hi, cam, 0.5)
+    b = oracle.render(vol, boxes, tf, lo, hi, cam, 0.5, opacity_ref_step=0.5)
+    np.testing.assert_array_equal(a["img"], b["img"])
