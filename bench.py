@@ -46,7 +46,8 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="paper", choices=["paper", "small", "precision", "grad", "batch"])
+    ap.add_argument("--workload", default="paper",
+                    choices=["paper", "small", "precision", "grad", "batch", "stream"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -661,8 +662,83 @@ def run_batch(a):
     print(json.dumps(line))
 
 
+def run_stream(a):
+    """Time-step streaming: 8 time steps of a 512^3 float32 field (advected blobs
+    + lattice noise, seed 3) in pinned host memory, 36 bricks, 2 device slots;
+    each step renders 4 orbit views at 1920x1080 (ERT 0.99) while the next step
+    is uploaded and packed on a copy stream. Compared with uploading each step
+    and only then rendering it."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2501_01628_gb300 import synth, vr
+    from paper_2501_01628_gb300.streaming import TimeSeriesRenderer
+    __graft_entry__.build()
+    n, steps = 512, 8
+    draws = synth.draw_fields(seed=3, n_fields=1)[0]
+    host = []
+    for t in range(steps):
+        host.append(synth.field_volume_torch(draws, t, n).cpu().pin_memory())
+    rng = np.random.default_rng(3)
+    tf = synth.random_tf(rng)
+    lo = min(float(h.min()) for h in host)
+    hi = max(float(h.max()) for h in host)
+    part = dict(kind="grid", grid=(4, 3, 3))
+    cams = [synth.orbit_camera(1920, 1080, az) for az in (0.0, 90.0, 180.0, 270.0)]
+    ctx = vr.vr_create(0)
+    vr.vr_set_transfer_function(ctx, tf, lo, hi)
+    vr.vr_set_render_params(ctx, 0.5, 0.99)
+    outs = [torch.empty((1080, 1920, 4), device="cuda") for _ in cams]
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    r = TimeSeriesRenderer(ctx, host, part, slots=2)
+    for t in range(2):  # warm
+        r.render_step(t, cams, outs)
+    r.close()
+    res = {}
+    for prefetch in (True, False):
+        r = TimeSeriesRenderer(ctx, host, part, slots=2)
+
+        def run():
+            for t in range(steps):
+                r.render_step(t, cams, outs, prefetch=prefetch)
+                if not prefetch:
+                    # no overlap: wait for each step's upload before its renders
+                    torch.cuda.synchronize()
+        # the first two steps are resident at creation; time steps 0..7
+        res[prefetch] = timed(run)
+        r.close()
+    # upload + pack of one step alone
+    v = vr.vr_volume_create(ctx, host[0], "f32", part)
+    up_ms = timed(lambda: vr.vr_volume_update_async(v, host[1]))
+    vr.vr_volume_release(v)
+    vr.vr_destroy(ctx)
+    nbytes = host[0].numel() * 4
+    line = dict(metric=METRIC, value=steps * len(cams) / (res[True] / 1e3), unit="frames/s", n_gpus=1,
+                steps=steps, warmup=2, ms_per_step=res[True] / steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload="time-step streaming: 8 steps of 512^3 f32 in pinned host memory, 2 device "
+                                     "slots, 36 bricks, 4 views of 1920x1080 per step, ERT 0.99"),
+                overlapped_ms=res[True], sequential_ms=res[False], speedup_vs_sequential=res[False] / res[True],
+                upload_pack_ms_per_step=up_ms, upload_GBps=nbytes / (up_ms / 1e3) / 1e9,
+                device_budget_bytes_f32_quads="2 volumes", gpu_launches=steps * len(cams) * 2)
+    print(json.dumps(line))
+
+
 def main():
     a = args_parse()
+    if a.workload == "stream":
+        run_stream(a)
+        return
     if a.workload == "batch":
         run_batch(a)
         return

@@ -263,6 +263,14 @@ vr_status vr_batch_release(vr_batch batch);
  * in place, on `stream`; complete when the call returns. No allocation for a
  * device source. */
 vr_status vr_volume_update(vr_volume vol, const float *src, int src_on_device, void *stream);
+/* As vr_volume_update, but asynchronous on `stream`: for time-varying data
+ * streamed through a fixed device budget (Sec. 4: time steps are loaded and
+ * later evicted rather than all held in GPU memory), the next step is uploaded
+ * and packed on one stream while another renders. A host source must be pinned
+ * memory for the copy to overlap; it is staged in a device buffer of the
+ * volume's float32 size, allocated by the first such call and kept until
+ * vr_volume_release. Order renders after the update with events. */
+vr_status vr_volume_update_async(vr_volume vol, const float *src, int src_on_device, void *stream);
 /* Gradient of a loss on the frame that vr_render_frame would produce with the
  * context's current camera, transfer function and parameters (the paper renders
  * only forward; this is the chain rule through the readings stated at the top

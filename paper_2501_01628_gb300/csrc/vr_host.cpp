@@ -795,6 +795,23 @@ vr_status vr_volume_update(vr_volume vol, const float *src, int src_on_device, v
     return VR_OK;
 }
 
+vr_status vr_volume_update_async(vr_volume vol, const float *src, int src_on_device, void *stream)
+{
+    if (!vol || !src) return VR_ERR_ARG;
+    vr_ctx ctx = vol->ctx;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nvox = static_cast<size_t>(vol->dims[0]) * vol->dims[1] * vol->dims[2];
+    const float *dsrc = src;
+    if (!src_on_device) {
+        if (!vol->d_staging) VR_CUDA(ctx, cudaMalloc(&vol->d_staging, nvox * sizeof(float)));
+        VR_CUDA(ctx, cudaMemcpyAsync(vol->d_staging, src, nvox * sizeof(float), cudaMemcpyHostToDevice, s));
+        dsrc = vol->d_staging;
+    }
+    VR_CUDA(ctx, pack_bricks(vol, dsrc, s));
+    return VR_OK;
+}
+
 vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_dev, float *grad_tf_dev,
                              float *grad_density_dev, void *stream)
 {
@@ -851,6 +868,7 @@ vr_status vr_volume_release(vr_volume vol)
     if (!vol) return VR_ERR_ARG;
     DeviceGuard g(vol->ctx->device);
     cudaFree(vol->d_data);
+    cudaFree(vol->d_staging);
     vol->ctx->live_objects--;
     delete vol;
     return VR_OK;

@@ -90,6 +90,7 @@ struct vr_volume_s {
     std::vector<vr::host::KdNode> tree;  // node 0 = root
     void *d_data = nullptr;
     long long bytes = 0;
+    float *d_staging = nullptr;    // float32 source for asynchronous re-packs from host memory
 };
 
 namespace vr {

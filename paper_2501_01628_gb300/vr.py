@@ -37,7 +37,7 @@ EXPORTS = (
     "vr_set_kernel_timing", "vr_get_kernel_timing", "vr_render_frame_noalloc",
     "vr_volume_update", "vr_render_backward", "vr_batch_create", "vr_batch_launch",
     "vr_batch_autotune", "vr_batch_release", "vr_batch_configure", "vr_set_render_mode",
-    "vr_set_opacity_correction",
+    "vr_set_opacity_correction", "vr_volume_update_async",
 )
 
 
@@ -90,6 +90,7 @@ _SIG = {
                                      ctypes.c_float, ctypes.POINTER(vr_camera), ctypes.c_float,
                                      ctypes.c_float, _P, _P]),
     "vr_volume_update": (_I, [_P, _P, _I, _P]),
+    "vr_volume_update_async": (_I, [_P, _P, _I, _P]),
     "vr_batch_create": (_I, [_P, _I, _P, _P, _P, _I, _P, _P, ctypes.POINTER(_P)]),
     "vr_batch_launch": (_I, [_P, _P]),
     "vr_batch_autotune": (_I, [_P, _P, ctypes.c_char_p, _P]),
@@ -283,6 +284,12 @@ def vr_volume_update(vol, volume, stream=None):
     """Re-pack `vol` from a float32 [Nz, Ny, Nx] array (same dims)."""
     ptr, on_dev, keep = _ptr_and_loc(volume)
     _check(lib().vr_volume_update(vol, ptr, on_dev, _stream(stream)), None, "vr_volume_update")
+
+
+def vr_volume_update_async(vol, volume, stream=None):
+    """Asynchronous re-pack on `stream` (host sources should be pinned)."""
+    ptr, on_dev, keep = _ptr_and_loc(volume)
+    _check(lib().vr_volume_update_async(vol, ptr, on_dev, _stream(stream)), None, "vr_volume_update_async")
 
 
 def vr_render_backward(ctx, vol, grad_rgba, grad_tf, grad_density=None, stream=None):
