@@ -78,12 +78,19 @@ struct OwnedRun {
     int ka, kb;
 };
 
+// A pixel's primary ray in voxel units, its whole-volume interval [t_in, t_out)
+// and the rounding margin used for every brick's slab estimate. FP32, with the
+// same arithmetic for every brick, so that each lattice sample has one owner.
+struct Ray {
+    float ov[3], dv[3], inv[3];
+    float t_in, t_out;
+    int margin;
+    bool hit;
+};
+
 template <typename P>
-__device__ __forceinline__ void owned_run(const P &p, const BrickLaunch &B, int px, int py, OwnedRun &run)
+__device__ __forceinline__ void ray_setup(const P &p, int px, int py, Ray &ray)
 {
-    run.ka = 0;
-    run.kb = -1;
-    // primary ray (FP32; identical arithmetic for every brick)
     const float fx = (static_cast<float>(px) + 0.5f) * p.inv_W;
     const float fy = (static_cast<float>(py) + 0.5f) * p.inv_H;
     float o[3], d[3];
@@ -106,66 +113,87 @@ __device__ __forceinline__ void owned_run(const P &p, const BrickLaunch &B, int 
         for (int i = 0; i < 3; ++i) d[i] *= inv;
     }
     // voxel-space origin and direction; t stays in world units
-    float ov[3], dv[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        ov[i] = o[i] * p.nmax;
-        dv[i] = d[i] * p.nmax;
+        ray.ov[i] = o[i] * p.nmax;
+        ray.dv[i] = d[i] * p.nmax;
     }
-
-    // whole-volume interval [t_in, t_out) and this brick's slab interval
-    float t0 = 0.0f, t1 = 3.0e38f, b0 = 0.0f, b1 = 3.0e38f;
+    // whole-volume interval (uses only (0 - o)/d and (N - o)/d)
+    float t0 = 0.0f, t1 = 3.0e38f, dmin = 3.0e38f;
     bool hit = true;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        if (dv[i] == 0.0f) {
-            if (ov[i] < 0.0f || ov[i] > p.N[i]) hit = false;
-            if (ov[i] < static_cast<float>(B.lo[i]) || ov[i] > static_cast<float>(B.hi[i])) hit = false;
+        if (ray.dv[i] == 0.0f) {
+            ray.inv[i] = 0.0f;
+            if (ray.ov[i] < 0.0f || ray.ov[i] > p.N[i]) hit = false;
         } else {
-            const float inv = __frcp_rn(dv[i]);
-            float ta = (0.0f - ov[i]) * inv, tb = (p.N[i] - ov[i]) * inv;
+            const float inv = __frcp_rn(ray.dv[i]);
+            ray.inv[i] = inv;
+            const float ta = (0.0f - ray.ov[i]) * inv, tb = (p.N[i] - ray.ov[i]) * inv;
             t0 = fmaxf(t0, fminf(ta, tb));
             t1 = fminf(t1, fmaxf(ta, tb));
-            ta = (static_cast<float>(B.lo[i]) - ov[i]) * inv;
-            tb = (static_cast<float>(B.hi[i]) - ov[i]) * inv;
+            dmin = fminf(dmin, fabsf(ray.dv[i]));
+        }
+    }
+    ray.t_in = t0;
+    ray.t_out = t1;
+    ray.hit = hit && t0 < t1;
+    // slab estimates are widened by a margin covering FP32 rounding of the
+    // positions (large only for rays nearly parallel to a face)
+    ray.margin = 2 + static_cast<int>(fminf(1.0e6f, __fdividef(1.0e-6f * p.nmax, dmin * p.dt)));
+}
+
+// The samples brick B owns along `ray`: the slab estimate, made exact with the
+// ownership test itself (sample k is owned iff it lies before t_out and its cell
+// is in the brick).
+template <typename P>
+__device__ __forceinline__ void brick_run(const P &p, const BrickLaunch &B, const Ray &ray, OwnedRun &run)
+{
+    run.ka = 0;
+    run.kb = -1;
+    if (!ray.hit) return;
+    float b0 = 0.0f, b1 = 3.0e38f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (ray.dv[i] == 0.0f) {
+            if (ray.ov[i] < static_cast<float>(B.lo[i]) || ray.ov[i] > static_cast<float>(B.hi[i])) return;
+        } else {
+            const float ta = (static_cast<float>(B.lo[i]) - ray.ov[i]) * ray.inv[i];
+            const float tb = (static_cast<float>(B.hi[i]) - ray.ov[i]) * ray.inv[i];
             b0 = fmaxf(b0, fminf(ta, tb));
             b1 = fminf(b1, fmaxf(ta, tb));
         }
     }
-    // NOTE: the whole-volume t_in must not depend on the brick; it uses
-    // (0 - o)/d and (N - o)/d only, in the same order for every brick.
-    if (hit && t0 < t1 && b0 <= b1) {
-        const float t_in = t0, t_out = t1;
-        // Slab estimate of the samples this brick owns, widened by a margin that
-        // covers FP32 rounding of the positions (large only for rays nearly
-        // parallel to a face), then made exact with the ownership test itself.
-        float dmin = 3.0e38f;
+    if (!(b0 <= b1)) return;
+    const float t_in = ray.t_in, t_out = ray.t_out;
+    int ka = max(0, static_cast<int>(floorf((b0 - t_in) * p.inv_dt - 0.5f)) - ray.margin);
+    int kb = static_cast<int>(ceilf((fminf(b1, t_out) - t_in) * p.inv_dt - 0.5f)) + ray.margin;
+    auto owned = [&](int k) {
+        const float t = fmaf(static_cast<float>(k) + 0.5f, p.dt, t_in);
+        const float qxv = fmaf(t, ray.dv[0], ray.ov[0]);
+        const float qyv = fmaf(t, ray.dv[1], ray.ov[1]);
+        const float qzv = fmaf(t, ray.dv[2], ray.ov[2]);
+        return t < t_out && qxv >= B.own_lo[0] && qxv < B.own_hi[0] && qyv >= B.own_lo[1] && qyv < B.own_hi[1] &&
+               qzv >= B.own_lo[2] && qzv < B.own_hi[2];
+    };
+    while (ka <= kb && !owned(ka)) ++ka;
+    while (kb > ka && !owned(kb)) --kb;
+    // owned samples are contiguous along the ray: [ka, kb] are all owned
+    run.ka = ka;
+    run.kb = kb;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            if (dv[i] != 0.0f) dmin = fminf(dmin, fabsf(dv[i]));
-        const int margin = 2 + static_cast<int>(fminf(1.0e6f, __fdividef(1.0e-6f * p.nmax, dmin * p.dt)));
-        int ka = max(0, static_cast<int>(floorf((b0 - t_in) * p.inv_dt - 0.5f)) - margin);
-        int kb = static_cast<int>(ceilf((fminf(b1, t_out) - t_in) * p.inv_dt - 0.5f)) + margin;
-        // sample k is owned iff it lies before t_out and its cell is in the brick
-        // (same FP32 arithmetic for every brick: each sample has exactly one owner)
-        auto owned = [&](int k) {
-            const float t = fmaf(static_cast<float>(k) + 0.5f, p.dt, t_in);
-            const float qxv = fmaf(t, dv[0], ov[0]);
-            const float qyv = fmaf(t, dv[1], ov[1]);
-            const float qzv = fmaf(t, dv[2], ov[2]);
-            return t < t_out && qxv >= B.own_lo[0] && qxv < B.own_hi[0] && qyv >= B.own_lo[1] &&
-                   qyv < B.own_hi[1] && qzv >= B.own_lo[2] && qzv < B.own_hi[2];
-        };
-        while (ka <= kb && !owned(ka)) ++ka;
-        while (kb > ka && !owned(kb)) --kb;
-        run.ka = ka;
-        run.kb = kb;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            run.step[i] = dv[i] * p.dt;
-            run.base[i] = fmaf(t_in, dv[i], ov[i] - (static_cast<float>(B.lo[i]) - 0.5f));
-        }
+    for (int i = 0; i < 3; ++i) {
+        run.step[i] = ray.dv[i] * p.dt;
+        run.base[i] = fmaf(t_in, ray.dv[i], ray.ov[i] - (static_cast<float>(B.lo[i]) - 0.5f));
     }
+}
+
+template <typename P>
+__device__ __forceinline__ void owned_run(const P &p, const BrickLaunch &B, int px, int py, OwnedRun &run)
+{
+    Ray ray;
+    ray_setup(p, px, py, ray);
+    brick_run(p, B, ray, run);
 }
 
 // Front-to-back emission-absorption over one owned run (see include/vr.h):

@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(128) march_grad_kernel(const __grid_constant__
     const int local = item - B.item_begin;
     const int ty = local / B.tiles_x, tx = local - ty * B.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rx = tx * kTileW + (warp & 1) * 8 + (lane & 7);
-    const int ry = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    const int rx = tx * p.tile_w + (warp & 1) * p.pw + (lane & (p.pw - 1));
+    const int ry = ty * p.tile_h + (warp >> 1) * (32 / p.pw) + lane / p.pw;
     float4 gp = make_float4(0.f, 0.f, 0.f, 0.f);
     if (rx < B.rect[2] && ry < B.rect[3]) gp = ga.grad_partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx];
     dev::OwnedRun run;

@@ -368,6 +368,10 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
     long long px = 0;
     int items = 0;
     std::memset(&mp, 0, sizeof(mp));
+    const int pw = ctx->packet_width, tile_w = 2 * pw, tile_h = 2 * (32 / pw);
+    mp.pw = pw;
+    mp.tile_w = tile_w;
+    mp.tile_h = tile_h;
     for (int b = 0; b < nb; ++b) {
         int *r = &fr.rects[4 * b];
         footprint(c, B, &vol->boxes[6 * b], nmax, r);
@@ -388,8 +392,8 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
         std::memcpy(L.rect, r, sizeof(L.rect));
         L.poff = fr.poff[b];
         L.item_begin = items;
-        L.tiles_x = (r[2] + kTileW - 1) / kTileW;
-        const int tiles_y = (r[3] + kTileH - 1) / kTileH;
+        L.tiles_x = (r[2] + tile_w - 1) / tile_w;
+        const int tiles_y = (r[3] + tile_h - 1) / tile_h;
         items += L.tiles_x * tiles_y;
     }
     fr.total_px = px;
@@ -513,24 +517,78 @@ vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s)
     return VR_OK;
 }
 
+// Staging image for a host output. Synchronous mode: one buffer, the caller's
+// stream waits for the copy. Asynchronous mode: two buffers used in turn; the
+// render stream first waits until the buffer's previous copy is done.
+vr_status host_staging(vr_ctx ctx, long long px, cudaStream_t s, float4 **buf, int *slot)
+{
+    if (!ctx->host_async) {
+        if (px > ctx->img_cap) {
+            if (ctx->d_img) cudaFree(ctx->d_img);
+            ctx->d_img = nullptr;
+            ctx->img_cap = 0;
+            VR_CUDA(ctx, cudaMalloc(&ctx->d_img, static_cast<size_t>(px) * sizeof(float4)));
+            ctx->img_cap = px;
+        }
+        *buf = ctx->d_img;
+        *slot = -1;
+        return VR_OK;
+    }
+    if (!ctx->copy_stream) {
+        VR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            VR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_rendered[i], cudaEventDisableTiming));
+            VR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming));
+        }
+    }
+    if (px > ctx->img2_cap) {
+        VR_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(ctx->d_img2[i]);
+            ctx->d_img2[i] = nullptr;
+        }
+        ctx->img2_cap = 0;
+        for (int i = 0; i < 2; ++i)
+            VR_CUDA(ctx, cudaMalloc(&ctx->d_img2[i], static_cast<size_t>(px) * sizeof(float4)));
+        ctx->img2_cap = px;
+    }
+    const int k = ctx->img_next;
+    ctx->img_next ^= 1;
+    VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_copied[k], 0));
+    *buf = ctx->d_img2[k];
+    *slot = k;
+    return VR_OK;
+}
+
+// Copy a staged image to host memory: at once and waiting (synchronous mode),
+// or on the copy stream after the render (asynchronous mode; vr_sync waits).
+vr_status host_copy(vr_ctx ctx, float *out, const float4 *buf, int slot, long long px, cudaStream_t s)
+{
+    const size_t bytes = static_cast<size_t>(px) * sizeof(float4);
+    if (slot < 0) {
+        VR_CUDA(ctx, cudaMemcpyAsync(out, buf, bytes, cudaMemcpyDeviceToHost, s));
+        VR_CUDA(ctx, cudaStreamSynchronize(s));
+        return VR_OK;
+    }
+    VR_CUDA(ctx, cudaEventRecord(ctx->ev_rendered[slot], s));
+    VR_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_rendered[slot], 0));
+    VR_CUDA(ctx, cudaMemcpyAsync(out, buf, bytes, cudaMemcpyDeviceToHost, ctx->copy_stream));
+    VR_CUDA(ctx, cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
+    return VR_OK;
+}
+
 vr_status composite_to(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s)
 {
     if (!out) return fail(ctx, VR_ERR_ARG, "null output");
     const long long px = static_cast<long long>(fr.W) * fr.H;
     if (out_on_device) return composite(ctx, fr, reinterpret_cast<float4 *>(out), s);
-    if (px > ctx->img_cap) {
-        if (ctx->d_img) cudaFree(ctx->d_img);
-        ctx->d_img = nullptr;
-        ctx->img_cap = 0;
-        VR_CUDA(ctx, cudaMalloc(&ctx->d_img, static_cast<size_t>(px) * sizeof(float4)));
-        ctx->img_cap = px;
-    }
-    vr_status st = composite(ctx, fr, ctx->d_img, s);
+    float4 *buf = nullptr;
+    int slot = -1;
+    vr_status st = host_staging(ctx, px, s, &buf, &slot);
     if (st != VR_OK) return st;
-    VR_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_img, static_cast<size_t>(px) * sizeof(float4),
-                                 cudaMemcpyDeviceToHost, s));
-    VR_CUDA(ctx, cudaStreamSynchronize(s));
-    return VR_OK;
+    st = composite(ctx, fr, buf, s);
+    if (st != VR_OK) return st;
+    return host_copy(ctx, out, buf, slot, px, s);
 }
 
 // Ray-state cycling frame straight into the image (device or host output).
@@ -542,23 +600,15 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
     if (st != VR_OK) return st;
     const long long px = static_cast<long long>(mp.W) * mp.H;
     float4 *dst = reinterpret_cast<float4 *>(out);
+    int slot = -1;
     if (!out_on_device) {
-        if (px > ctx->img_cap) {
-            if (ctx->d_img) cudaFree(ctx->d_img);
-            ctx->d_img = nullptr;
-            ctx->img_cap = 0;
-            VR_CUDA(ctx, cudaMalloc(&ctx->d_img, static_cast<size_t>(px) * sizeof(float4)));
-            ctx->img_cap = px;
-        }
-        dst = ctx->d_img;
+        st = host_staging(ctx, px, s, &dst, &slot);
+        if (st != VR_OK) return st;
     }
     const int t = timing_begin(ctx, 0, s);
     VR_CUDA(ctx, launch_march_cycle(mp, vol->dtype, dst, s));
     timing_end(ctx, t, s);
-    if (!out_on_device) {
-        VR_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_img, static_cast<size_t>(px) * sizeof(float4), cudaMemcpyDeviceToHost, s));
-        VR_CUDA(ctx, cudaStreamSynchronize(s));
-    }
+    if (!out_on_device) return host_copy(ctx, out, dst, slot, px, s);
     return VR_OK;
 }
 
@@ -656,6 +706,13 @@ vr_status vr_destroy(vr_ctx ctx)
     cudaFree(ctx->d_gpart);
     cudaFree(ctx->frame.d_part);
     cudaFree(ctx->d_img);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(ctx->d_img2[i]);
+        if (ctx->ev_rendered[i]) cudaEventDestroy(ctx->ev_rendered[i]);
+        if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+    }
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (auto &t : ctx->timed) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
@@ -705,6 +762,7 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
     if (!ctx) return VR_ERR_ARG;
     DeviceGuard g(ctx->device);
     VR_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    if (ctx->copy_stream) VR_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
     int err = 0;
     VR_CUDA(ctx, cudaMemcpy(&err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
@@ -1067,6 +1125,22 @@ vr_status vr_set_opacity_correction(vr_ctx ctx, float ref_step_voxels)
     if (!(ref_step_voxels >= 0.0f) || !std::isfinite(ref_step_voxels))
         return fail(ctx, VR_ERR_ARG, "bad reference step");
     ctx->opc_ref = ref_step_voxels;
+    return VR_OK;
+}
+
+vr_status vr_set_host_output_async(vr_ctx ctx, int on)
+{
+    if (!ctx) return VR_ERR_ARG;
+    ctx->host_async = on != 0;
+    return VR_OK;
+}
+
+vr_status vr_set_packet_width(vr_ctx ctx, int packet_width)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (packet_width != 4 && packet_width != 8 && packet_width != 16)
+        return fail(ctx, VR_ERR_ARG, "packet width must be 4, 8 or 16");
+    ctx->packet_width = packet_width;
     return VR_OK;
 }
 

@@ -12,7 +12,9 @@ namespace vr {
 constexpr int kMaxBricks = VR_MAX_BRICKS;
 constexpr int kMaxFactors = 8;
 
-// March tile: 16 x 8 pixels per 128-thread block, four 8 x 4 warp packets.
+// Work item of the no-allocation march: 16 x 8 pixels per 128-thread block,
+// four 8 x 4 warp packets (the other marches take the packet width as a
+// parameter, MarchParams::pw).
 constexpr int kTileW = 16;
 constexpr int kTileH = 8;
 // Composite tile: 32 x 8 pixels per 256-thread block.
@@ -50,6 +52,8 @@ struct MarchParams {
     int ortho;
     int W, H;
     float inv_W, inv_H;  // 1/W, 1/H
+    int pw;              // ray packet: a warp marches pw x (32/pw) pixels (pw = 4, 8 or 16)
+    int tile_w, tile_h;  // work item: 2 x 2 packets = (2 pw) x (64/pw) pixels
     // volume
     float nmax;         // voxels per world unit
     float N[3];         // volume extent in voxels

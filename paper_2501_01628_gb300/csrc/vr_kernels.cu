@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     const int local = item - B.item_begin;
     const int ty = local / B.tiles_x, tx = local - ty * B.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rx = tx * kTileW + (warp & 1) * 8 + (lane & 7);
-    const int ry = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    const int rx = tx * p.tile_w + (warp & 1) * p.pw + (lane & (p.pw - 1));
+    const int ry = ty * p.tile_h + (warp >> 1) * (32 / p.pw) + lane / p.pw;
     if (rx >= B.rect[2] || ry >= B.rect[3]) return;
     const int px = B.rect[0] + rx, py = B.rect[1] + ry;
 
@@ -84,17 +84,19 @@ template <typename S, bool COUNT, bool OPC>
 __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant__ MarchParams p, float4 *out)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
-    const int py = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    const int px = blockIdx.x * p.tile_w + (warp & 1) * p.pw + (lane & (p.pw - 1));
+    const int py = blockIdx.y * p.tile_h + (warp >> 1) * (32 / p.pw) + lane / p.pw;
     if (px >= p.W || py >= p.H) return;
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
     unsigned long long executed = 0;
-    for (int j = 0; j < p.nb; ++j) {
+    dev::Ray ray;
+    dev::ray_setup(p, px, py, ray);  // once per pixel; each brick only intersects it
+    for (int j = 0; ray.hit && j < p.nb; ++j) {
         const BrickLaunch &B = p.b[p.order[j]];
         if (px < B.rect[0] || px >= B.rect[0] + B.rect[2] || py < B.rect[1] || py >= B.rect[1] + B.rect[3])
             continue;
         dev::OwnedRun run;
-        dev::owned_run(p, B, px, py, run);
+        dev::brick_run(p, B, ray, run);
         dev::march_accumulate<S, COUNT, OPC>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, C0, C1,
                                              C2, T, executed, p.opc_ratio);
         if (T <= p.ert_T) break;
@@ -243,7 +245,7 @@ cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s)
 cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out, cudaStream_t s)
 {
     if (p.W <= 0 || p.H <= 0) return cudaSuccess;
-    const dim3 grid((p.W + kTileW - 1) / kTileW, (p.H + kTileH - 1) / kTileH);
+    const dim3 grid((p.W + p.tile_w - 1) / p.tile_w, (p.H + p.tile_h - 1) / p.tile_h);
     const bool count = p.sample_counter != nullptr;
     const bool opc = p.opc_ratio != 1.0f;
 #define VR_CYCLE(T)                                                                                    \

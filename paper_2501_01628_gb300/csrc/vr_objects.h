@@ -62,6 +62,7 @@ struct vr_ctx_s {
     std::vector<int> factors;
     int mode = 0;                  // 0: sort-last partials + composite; 1: ray-state cycling
     float opc_ref = 0.0f;          // opacity-correction reference step in voxels (0: off)
+    int packet_width = 4;          // ray packet of the march: pw x (32/pw) pixels per warp
     unsigned long long *d_counter = nullptr;
     int *d_error = nullptr;        // device error word (vr_sync reports and clears it)
     bool count_samples = false;
@@ -70,6 +71,14 @@ struct vr_ctx_s {
     vr_frame_s frame;              // context-owned frame for vr_render_frame
     float4 *d_img = nullptr;       // staging for host outputs
     long long img_cap = 0;
+    // asynchronous host output: two staging images, copies on their own stream
+    bool host_async = false;
+    float4 *d_img2[2] = {nullptr, nullptr};
+    long long img2_cap = 0;
+    int img_next = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_rendered[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
     int live_objects = 0;
     // kernel timing (vr_set_kernel_timing)
     bool timing = false;

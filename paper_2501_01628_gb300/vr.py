@@ -37,7 +37,8 @@ EXPORTS = (
     "vr_set_kernel_timing", "vr_get_kernel_timing", "vr_render_frame_noalloc",
     "vr_volume_update", "vr_render_backward", "vr_batch_create", "vr_batch_launch",
     "vr_batch_autotune", "vr_batch_release", "vr_batch_configure", "vr_set_render_mode",
-    "vr_set_opacity_correction", "vr_volume_update_async",
+    "vr_set_opacity_correction", "vr_volume_update_async", "vr_set_packet_width",
+    "vr_set_host_output_async",
 )
 
 
@@ -98,6 +99,8 @@ _SIG = {
     "vr_batch_configure": (_I, [_P, _I, _I, _I]),
     "vr_set_render_mode": (_I, [_P, _I]),
     "vr_set_opacity_correction": (_I, [_P, ctypes.c_float]),
+    "vr_set_packet_width": (_I, [_P, _I]),
+    "vr_set_host_output_async": (_I, [_P, _I]),
     "vr_render_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
     "vr_plan_view": (_I, [_P, ctypes.POINTER(vr_partition), ctypes.POINTER(vr_camera), _P, _P]),
@@ -370,6 +373,16 @@ def vr_set_composite_schedule(ctx, factors=()):
 def vr_set_opacity_correction(ctx, ref_step_voxels: float):
     """alpha' = 1 - (1 - alpha)^(step / ref_step) per sample; 0 turns it off."""
     _check(lib().vr_set_opacity_correction(ctx, float(ref_step_voxels)), ctx, "vr_set_opacity_correction")
+
+
+def vr_set_host_output_async(ctx, on: bool):
+    """Host outputs return at once; images land in host memory by vr_sync."""
+    _check(lib().vr_set_host_output_async(ctx, int(bool(on))), ctx, "vr_set_host_output_async")
+
+
+def vr_set_packet_width(ctx, packet_width: int):
+    """Warp ray packet packet_width x (32/packet_width) pixels (4, 8 or 16)."""
+    _check(lib().vr_set_packet_width(ctx, int(packet_width)), ctx, "vr_set_packet_width")
 
 
 def vr_set_render_mode(ctx, mode: int):

@@ -214,3 +214,33 @@ def test_error_paths(vr):
         vr.vr_volume_release(v)
     finally:
         vr.vr_destroy(ctx)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_async_host_output_equals_device_output(vr, mode):
+    import torch
+    vol, tf = synth.small_blob_scene(n=32)
+    lo, hi = synth.volume_range(vol)
+    cams = [synth.orbit_camera(64, 48, az) for az in (20.0, 140.0, 260.0, 300.0)]
+    ctx = vr.vr_create(0)
+    v = vr.vr_volume_create(ctx, vol, "f32", dict(kind="grid", grid=(2, 2, 2)))
+    try:
+        vr.vr_set_transfer_function(ctx, tf, lo, hi)
+        vr.vr_set_render_mode(ctx, mode)
+        refs = []
+        for c in cams:
+            vr.vr_set_camera(ctx, c)
+            o = torch.empty((48, 64, 4), device="cuda")
+            vr.vr_render_frame(ctx, v, o)
+            refs.append(o.cpu())
+        vr.vr_set_host_output_async(ctx, True)
+        hosts = [torch.full((48, 64, 4), float("nan")).pin_memory() for _ in cams]
+        for c, h in zip(cams, hosts):
+            vr.vr_set_camera(ctx, c)
+            vr.vr_render_frame(ctx, v, h)
+        vr.vr_sync(ctx)
+        for h, r in zip(hosts, refs):
+            assert torch.equal(h, r)
+    finally:
+        vr.vr_volume_release(v)
+        vr.vr_destroy(ctx)
