@@ -83,7 +83,7 @@ def recorded_traffic():
     try:
         text = open(path).read()
         h = hashlib.sha256()
-        for f in ("vr_kernels.cu", "vr_internal.h"):
+        for f in ("vr_kernels.cu", "vr_device.cuh", "vr_internal.h"):
             h.update(open(os.path.join(csrc, f), "rb").read())
     except OSError:
         return None
@@ -429,8 +429,8 @@ def run_ours(a):
                       traffic=recorded_traffic() if a.workload == "paper" else None,
                       note="FP32 %d flops/sample x executed samples / mean march launch; peak = 152 SMs x "
                            "128 lanes x 2 x %.0f MHz (derived)" % (FLOPS_PER_SAMPLE, sm_max)),
-        roofline_l1=dict(note="ncu: L1 data-pipe LSU wavefronts 90% of peak on the march "
-                              "(profiles/march_paper_workload.md): the unit that binds it"),
+        roofline_l1=dict(note="ncu on the march: L1 data-pipe LSU wavefronts 70% of peak, SM issue "
+                              "67%, top stall long scoreboard (profiles/march_paper_workload.md)"),
         roofline_hbm=dict(march=dict(achieved=march_hbm_gbs, peak=hbm, unit="GB/s", frac=march_hbm_gbs / hbm,
                                      note="compulsory bytes (volume once + partial writes) / march time, %s"
                                           % hbm_src),
