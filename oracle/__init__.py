@@ -15,6 +15,10 @@ Parity pins (checked in ``tests/test_oracle_pins.py``):
   P5 exact trilinear weights on the axis-aligned 64^3 / 256^2 lattice with a
      linear ramp volume (closed form)
   P6 range / alpha-0 / alpha-1 / identity invariants
+Mesh pins (``tests/test_oracle_mesh.py``): linear fields reproduced exactly,
+barycentric partition of unity and containment, bins equal brute force, mesh
+renders equal the pinned voxel renders on rays along shared grid lines, the
+constant-slab closed form, and brick-split associativity.
 """
 from __future__ import annotations
 
@@ -62,7 +66,28 @@ class _Scene(ctypes.Structure):
                 ("step_voxels", ctypes.c_double), ("ert_alpha", ctypes.c_double),
                 ("ert_bias", ctypes.c_double), ("end_bias", ctypes.c_double),
                 ("tf64", ctypes.c_void_p), ("ert_global", ctypes.c_int),
-                ("opc_ratio", ctypes.c_double)]
+                ("opc_ratio", ctypes.c_double), ("mesh_verts", ctypes.c_void_p),
+                ("mesh_vals", ctypes.c_void_p), ("mesh_tets", ctypes.c_void_p),
+                ("mesh_nt", ctypes.c_longlong), ("mesh_nv", ctypes.c_int),
+                ("mesh_bruteforce", ctypes.c_int)]
+
+
+class Mesh:
+    """Tetrahedral-mesh input in place of a voxel volume.
+
+    verts (nv, 3) world positions, vals (nv,) vertex values, tets (nt, 4)
+    vertex indices, dims the nominal lattice (Nx, Ny, Nz) that fixes the domain
+    box [0, dims/Nmax], the lattice spacing and the ownership cells. float32
+    inputs are converted to double exactly."""
+
+    def __init__(self, verts, vals, tets, dims, bruteforce: bool = False):
+        self.verts = np.ascontiguousarray(np.asarray(verts, dtype=np.float64).reshape(-1, 3))
+        self.vals = np.ascontiguousarray(np.asarray(vals, dtype=np.float64).ravel())
+        self.tets = np.ascontiguousarray(np.asarray(tets, dtype=np.int32).reshape(-1, 4))
+        self.dims = tuple(int(d) for d in dims)
+        self.bruteforce = bool(bruteforce)
+        if self.vals.size != self.verts.shape[0]:
+            raise ValueError("one value per vertex")
 
 
 def lib():
@@ -87,6 +112,10 @@ def lib():
             _lib.orc_classify.argtypes = [ctypes.POINTER(_Scene), ctypes.c_double, ctypes.c_void_p]
             _lib.orc_primary_ray.argtypes = [ctypes.POINTER(_Camera), ctypes.c_int, ctypes.c_int,
                                              ctypes.c_void_p, ctypes.c_void_p]
+            _lib.orc_mesh_sample.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]
+            _lib.orc_mesh_sample.restype = ctypes.c_int
     return _lib
 
 
@@ -139,6 +168,10 @@ def _dtype_code(vol: np.ndarray, dtype):
 
 
 def _scene(vol, boxes, tf, vmin, vmax, cam, step_voxels, ert_alpha, dtype, keep):
+    mesh = vol if isinstance(vol, Mesh) else None
+    if mesh is not None:
+        keep.append(mesh)
+        vol = np.zeros((1, 1, 1), np.float32)
     vol = np.ascontiguousarray(vol)
     code = _dtype_code(vol, dtype)
     boxes = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 6)
@@ -161,6 +194,14 @@ def _scene(vol, boxes, tf, vmin, vmax, cam, step_voxels, ert_alpha, dtype, keep)
     sc.step_voxels = float(step_voxels)
     sc.ert_alpha = float(ert_alpha)
     sc.tf64 = tf64.ctypes.data if tf64 is not None else None
+    if mesh is not None:
+        sc.dims[:] = list(mesh.dims)
+        sc.mesh_verts = mesh.verts.ctypes.data
+        sc.mesh_vals = mesh.vals.ctypes.data
+        sc.mesh_tets = mesh.tets.ctypes.data
+        sc.mesh_nt = mesh.tets.shape[0]
+        sc.mesh_nv = mesh.verts.shape[0]
+        sc.mesh_bruteforce = int(mesh.bruteforce)
     return sc
 
 
@@ -176,6 +217,25 @@ def sample(vol, points, dtype=None) -> np.ndarray:
     pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
     return np.array([lib().orc_sample(ctypes.byref(sc), pts[i].ctypes.data)
                      for i in range(pts.shape[0])])
+
+
+def mesh_sample(mesh: Mesh, boxes, points) -> dict:
+    """Mesh value at world points (m, 3): per point the owner brick (cell rule),
+    the value from that brick's elements, the chosen element and its smallest
+    barycentric coordinate."""
+    keep = []
+    sc = _scene(mesh, boxes, np.zeros((2, 4), np.float32), 0.0, 1.0, _DUMMY_CAM, 0.5, 1.0, None, keep)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    m = pts.shape[0]
+    vals = np.zeros(m)
+    elem = np.zeros(m, np.int64)
+    minb = np.zeros(m)
+    brick = np.zeros(m, np.int32)
+    rc = lib().orc_mesh_sample(ctypes.byref(sc), m, pts.ctypes.data, vals.ctypes.data, elem.ctypes.data,
+                               minb.ctypes.data, brick.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("oracle mesh sample failed (%d)" % rc)
+    return dict(vals=vals, elem=elem, minb=minb, brick=brick)
 
 
 def classify(tf, vmin, vmax, values) -> np.ndarray:
@@ -205,7 +265,8 @@ def render(vol: np.ndarray, boxes, tf: np.ndarray, vmin: float, vmax: float, cam
            opacity_ref_step: float = 0.0):
     """Render pixels with the FP64 oracle.
 
-    vol     [Nz, Ny, Nx] array (float32/float64, or uint16 bits with dtype BF16/F16)
+    vol     [Nz, Ny, Nx] array (float32/float64, or uint16 bits with dtype BF16/F16),
+            or a Mesh (tetrahedral elements)
     boxes   (nb, 6) int half-open voxel boxes (lo xyz, hi xyz)
     pixels  (m, 2) int (px, py) list, or crop = (x0, y0, w, h); default = full image
     Returns dict(img=(m,4) or (h,w,4), partials=(nb, ...,4) or None, nsamples=int).

@@ -58,6 +58,15 @@ typedef struct {
     const double *tf64;     /* optional: ntf x 4 table in double, used instead of tf */
     int ert_global;         /* ray-state cycling: one (C, T) along the whole ray, global termination */
     double opc_ratio;       /* opacity correction step/reference step; 0 or 1 = off */
+    /* tetrahedral mesh (unstructured elements). When mesh_tets is set the
+     * samples come from the mesh and vol/dtype are unused; dims still fix the
+     * domain box, the lattice spacing and the ownership cells. */
+    const double *mesh_verts; /* nv x 3 world positions */
+    const double *mesh_vals;  /* nv vertex values */
+    const int *mesh_tets;     /* nt x 4 vertex indices */
+    long long mesh_nt;
+    int mesh_nv;
+    int mesh_bruteforce;      /* 1: search every element of the brick (no bins) */
 } orc_scene;
 
 /* ---- scalar helpers ---------------------------------------------------- */
@@ -131,6 +140,195 @@ static double sample_trilinear(const orc_scene *sc, const double p[3])
                 s += w * voxel(sc, idx);
             }
     return s;
+}
+
+/* ---- sampling: tetrahedral mesh (unstructured elements) ----------------
+ * The paper's data set is a mixed finite-element mesh distributed over ranks
+ * (Sec. 5); here elements are tetrahedra, each held by one brick (rank).
+ * Readings (the paper is silent on the sampling rule):
+ *   - element e belongs to the brick whose box contains its centroid's cell
+ *     clamp(floor(centroid Nmax), 0, N-1);
+ *   - a lattice sample keeps the owner of Sec. 2.2's reading (its cell's
+ *     brick) and takes its value from the owner's elements: the linear
+ *     interpolant sum_i lambda_i s_i of the element that maximises
+ *     min_i lambda_i(p), the barycentric coordinates of p. For p inside an
+ *     element that is the element; on a shared face every candidate gives the
+ *     same value (the interpolant is continuous on a conforming mesh); p
+ *     outside every element by rounding takes the nearest one.
+ * Barycentrics by Cramer's rule on the edge matrix [v1-v0, v2-v0, v3-v0]. */
+static void cross3(const double a[3], const double b[3], double o[3]);
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static double det3(const double a[3], const double b[3], const double c[3])
+{
+    double bc[3];
+    cross3(b, c, bc);
+    return dot3(a, bc);
+}
+
+static double tet_bary(const orc_scene *sc, long long e, const double p[3], double lam[4])
+{
+    const int *t = sc->mesh_tets + 4 * e;
+    const double *v0 = sc->mesh_verts + 3 * (long long)t[0];
+    double a[3], b[3], c[3], r[3];
+    for (int i = 0; i < 3; ++i) {
+        a[i] = sc->mesh_verts[3 * (long long)t[1] + i] - v0[i];
+        b[i] = sc->mesh_verts[3 * (long long)t[2] + i] - v0[i];
+        c[i] = sc->mesh_verts[3 * (long long)t[3] + i] - v0[i];
+        r[i] = p[i] - v0[i];
+    }
+    const double det = det3(a, b, c);
+    lam[1] = det3(r, b, c) / det;
+    lam[2] = det3(a, r, c) / det;
+    lam[3] = det3(a, b, r) / det;
+    lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+    double m = lam[0];
+    for (int i = 1; i < 4; ++i)
+        if (lam[i] < m) m = lam[i];
+    return m;
+}
+
+/* Element lists: by brick, and by a uniform grid of bins over the domain box
+ * (each element in every bin its bounding box, widened by 1e-9, overlaps). The
+ * bins only narrow the candidates: an element whose closed box misses p has a
+ * negative coordinate at p and cannot beat the element containing p. */
+typedef struct {
+    int *brick;          /* nt */
+    long long *bstart;   /* nb + 1 */
+    int *bitems;
+    int r[3];
+    double E[3];
+    long long *start;    /* bins + 1 */
+    int *items;
+} mesh_index;
+
+static void mesh_index_free(mesh_index *mi)
+{
+    free(mi->brick); free(mi->bstart); free(mi->bitems); free(mi->start); free(mi->items);
+    memset(mi, 0, sizeof(*mi));
+}
+
+static int in_box(const int *box, const int c[3]);
+
+static int mesh_bin(const mesh_index *mi, int a, double x)
+{
+    return clampi((long long)floor(x / mi->E[a] * mi->r[a]), 0, mi->r[a] - 1);
+}
+
+/* Returns 0, -1 on allocation failure, -2 on a bad element index. */
+static int mesh_index_build(const orc_scene *sc, mesh_index *mi)
+{
+    memset(mi, 0, sizeof(*mi));
+    const long long nt = sc->mesh_nt;
+    const int nb = sc->nb, nm = nmax3(sc->dims);
+    for (long long e = 0; e < 4 * nt; ++e)
+        if (sc->mesh_tets[e] < 0 || sc->mesh_tets[e] >= sc->mesh_nv) return -2;
+    mi->brick = (int *)malloc(sizeof(int) * (nt > 0 ? nt : 1));
+    mi->bstart = (long long *)calloc(nb + 1, sizeof(long long));
+    mi->bitems = (int *)malloc(sizeof(int) * (nt > 0 ? nt : 1));
+    if (!mi->brick || !mi->bstart || !mi->bitems) { mesh_index_free(mi); return -1; }
+    for (long long e = 0; e < nt; ++e) {
+        int c[3];
+        for (int a = 0; a < 3; ++a) {
+            double m = 0.0;
+            for (int j = 0; j < 4; ++j) m += sc->mesh_verts[3 * (long long)sc->mesh_tets[4 * e + j] + a];
+            c[a] = clampi((long long)floor(m / 4.0 * nm), 0, sc->dims[a] - 1);
+        }
+        mi->brick[e] = -1;
+        for (int b = 0; b < nb; ++b)
+            if (in_box(sc->boxes + 6 * b, c)) { mi->brick[e] = b; break; }
+        if (mi->brick[e] >= 0) mi->bstart[mi->brick[e] + 1]++;
+    }
+    for (int b = 0; b < nb; ++b) mi->bstart[b + 1] += mi->bstart[b];
+    {
+        long long *fill = (long long *)malloc(sizeof(long long) * (nb + 1));
+        if (!fill) { mesh_index_free(mi); return -1; }
+        memcpy(fill, mi->bstart, sizeof(long long) * (nb + 1));
+        for (long long e = 0; e < nt; ++e)
+            if (mi->brick[e] >= 0) mi->bitems[fill[mi->brick[e]]++] = (int)e;
+        free(fill);
+    }
+    double side = cbrt((double)(nt > 2 ? nt : 2) / 2.0);
+    for (int a = 0; a < 3; ++a) {
+        mi->E[a] = (double)sc->dims[a] / nm;
+        int r = (int)ceil(side * mi->E[a]);
+        mi->r[a] = r < 1 ? 1 : (r > 128 ? 128 : r);
+    }
+    const long long nbins = (long long)mi->r[0] * mi->r[1] * mi->r[2];
+    mi->start = (long long *)calloc(nbins + 1, sizeof(long long));
+    if (!mi->start) { mesh_index_free(mi); return -1; }
+    const double eps = 1e-9;
+    for (int pass = 0; pass < 2; ++pass) {
+        long long *fill = NULL;
+        if (pass == 1) {
+            for (long long i = 0; i < nbins; ++i) mi->start[i + 1] += mi->start[i];
+            mi->items = (int *)malloc(sizeof(int) * (mi->start[nbins] > 0 ? mi->start[nbins] : 1));
+            fill = (long long *)malloc(sizeof(long long) * (nbins + 1));
+            if (!mi->items || !fill) { free(fill); mesh_index_free(mi); return -1; }
+            memcpy(fill, mi->start, sizeof(long long) * (nbins + 1));
+        }
+        for (long long e = 0; e < nt; ++e) {
+            int blo[3], bhi[3];
+            for (int a = 0; a < 3; ++a) {
+                double lo = INFINITY, hi = -INFINITY;
+                for (int j = 0; j < 4; ++j) {
+                    double x = sc->mesh_verts[3 * (long long)sc->mesh_tets[4 * e + j] + a];
+                    if (x < lo) lo = x;
+                    if (x > hi) hi = x;
+                }
+                blo[a] = mesh_bin(mi, a, lo - eps);
+                bhi[a] = mesh_bin(mi, a, hi + eps);
+            }
+            for (int z = blo[2]; z <= bhi[2]; ++z)
+                for (int y = blo[1]; y <= bhi[1]; ++y)
+                    for (int x = blo[0]; x <= bhi[0]; ++x) {
+                        long long bin = ((long long)z * mi->r[1] + y) * mi->r[0] + x;
+                        if (pass == 0) mi->start[bin + 1]++;
+                        else mi->items[fill[bin]++] = (int)e;
+                    }
+        }
+        free(fill);
+    }
+    return 0;
+}
+
+/* Value at p from brick `brick`'s elements; *gap is set when p lies in none of
+ * them by more than rounding (smallest barycentric below -1e-5: the elements
+ * do not tile the brick). The chosen
+ * element and its smallest barycentric coordinate go to *elem and *minb. */
+static double sample_mesh(const orc_scene *sc, const mesh_index *mi, int brick, const double p[3],
+                          int *gap, long long *elem, double *minb)
+{
+    const int *items = mi->bitems;
+    long long lo = mi->bstart[brick], hi = mi->bstart[brick + 1];
+    if (!sc->mesh_bruteforce) {
+        long long bin = ((long long)mesh_bin(mi, 2, p[2]) * mi->r[1] + mesh_bin(mi, 1, p[1])) * mi->r[0] +
+                        mesh_bin(mi, 0, p[0]);
+        items = mi->items;
+        lo = mi->start[bin];
+        hi = mi->start[bin + 1];
+    }
+    double best = -INFINITY, val = 0.0;
+    long long be = -1;
+    for (long long i = lo; i < hi; ++i) {
+        const long long e = items[i];
+        if (mi->brick[e] != brick) continue;
+        double lam[4];
+        const double m = tet_bary(sc, e, p, lam);
+        if (m > best) {
+            best = m;
+            be = e;
+            val = 0.0;
+            for (int j = 0; j < 4; ++j) val += lam[j] * sc->mesh_vals[sc->mesh_tets[4 * e + j]];
+        }
+    }
+    /* float32 vertices on a brick plane lo/Nmax that is not a binary fraction
+     * sit up to ~1e-7 of an element off the plane; a real hole is far larger */
+    if (!(best >= -1e-5)) *gap = 1;
+    if (elem) *elem = be;
+    if (minb) *minb = best;
+    return val;
 }
 
 /* ---- classification: 1D RGBA transfer function ------------------------
@@ -252,7 +450,15 @@ typedef struct {
     char *done;     /* nb */
     int *order;     /* nb */
     int bad;        /* set when a sample's cell lies in no brick */
+    const mesh_index *mi; /* element lists when the scene is a mesh */
+    int gap;        /* set when a mesh sample lies in none of its brick's elements */
 } pixel_ws;
+
+static double sample_at(const orc_scene *sc, pixel_ws *ws, int brick, const double p[3])
+{
+    if (sc->mesh_tets) return sample_mesh(sc, ws->mi, brick, p, &ws->gap, NULL, NULL);
+    return sample_trilinear(sc, p);
+}
 
 static long long render_pixel(const orc_scene *sc, int px, int py, pixel_ws *ws,
                               double out[4], double *partials_px, long long pstride)
@@ -301,7 +507,7 @@ static long long render_pixel(const orc_scene *sc, int px, int py, pixel_ws *ws,
                  * falls to the threshold */
                 if (gdone) break;
                 double rgba[4];
-                classify(sc, sample_trilinear(sc, p), rgba);
+                classify(sc, sample_at(sc, ws, cur, p), rgba);
                 for (int ch = 0; ch < 3; ++ch) out[ch] += gT * rgba[3] * rgba[ch];
                 gT *= 1.0 - rgba[3];
                 ++executed;
@@ -310,7 +516,7 @@ static long long render_pixel(const orc_scene *sc, int px, int py, pixel_ws *ws,
             }
             if (ws->done[cur]) continue;
             double rgba[4];
-            classify(sc, sample_trilinear(sc, p), rgba);
+            classify(sc, sample_at(sc, ws, cur, p), rgba);
             double Tb = ws->T[cur];
             for (int ch = 0; ch < 3; ++ch) ws->C[3 * cur + ch] += Tb * rgba[3] * rgba[ch];
             ws->T[cur] = Tb * (1.0 - rgba[3]);
@@ -359,7 +565,8 @@ partials:
  *   partials nb x m x 4 per-brick partials (may be NULL)
  *   nsamples executed sample count over the list (may be NULL)
  * Returns 0 on success, -1 on allocation failure, -2 on bad arguments, -4 if
- * a sample fell in a cell that no brick covers (the boxes do not tile). */
+ * a sample fell in a cell that no brick covers (the boxes do not tile), -5 if
+ * a mesh sample lay in none of its brick's elements (they do not tile it). */
 int orc_render_pixels(const orc_scene *sc, int m, const int *pix, double *img,
                       double *partials, long long *nsamples, int nthreads)
 {
@@ -368,9 +575,17 @@ int orc_render_pixels(const orc_scene *sc, int m, const int *pix, double *img,
     long long total = 0;
     int fail = 0;
     if (nthreads < 1) nthreads = 1;
+    mesh_index mi;
+    memset(&mi, 0, sizeof(mi));
+    if (sc->mesh_tets) {
+        int rc = mesh_index_build(sc, &mi);
+        if (rc) return rc;
+    }
 #pragma omp parallel num_threads(nthreads) reduction(+ : total) reduction(| : fail)
     {
         pixel_ws ws;
+        ws.mi = &mi;
+        ws.gap = 0;
         const int nb = sc->nb;
         ws.C = (double *)malloc(sizeof(double) * 3 * nb);
         ws.T = (double *)malloc(sizeof(double) * nb);
@@ -387,12 +602,15 @@ int orc_render_pixels(const orc_scene *sc, int m, const int *pix, double *img,
                                       partials ? partials + 4 * (long long)i : NULL,
                                       4 * (long long)m);
             if (ws.bad) fail |= 2;
+            if (ws.gap) fail |= 4;
         }
         free(ws.C); free(ws.T); free(ws.first); free(ws.done); free(ws.order);
     }
+    mesh_index_free(&mi);
     if (nsamples) *nsamples = total;
     if (fail & 1) return -1;
-    return (fail & 2) ? -4 : 0;
+    if (fail & 2) return -4;
+    return (fail & 4) ? -5 : 0;
 }
 
 /* ---- partitions (Sec. 2.2 spatial distribution; Sec. 4 uneven shares) ----
@@ -514,7 +732,7 @@ int orc_render_grad(const orc_scene *sc, int m, const int *pix, const double *gr
                     double *grad_vol, int nthreads)
 {
     if (!sc || sc->nb < 1 || sc->ntf < 2 || !(sc->vmax > sc->vmin) || sc->step_voxels <= 0 ||
-        sc->ert_alpha < 1.0 || (sc->opc_ratio > 0.0 && sc->opc_ratio != 1.0))
+        sc->ert_alpha < 1.0 || (sc->opc_ratio > 0.0 && sc->opc_ratio != 1.0) || sc->mesh_tets)
         return -2;
     const int nm = nmax3(sc->dims);
     const double E[3] = {(double)sc->dims[0] / nm, (double)sc->dims[1] / nm, (double)sc->dims[2] / nm};
@@ -628,6 +846,32 @@ int orc_render_grad(const orc_scene *sc, int m, const int *pix, const double *gr
         free(rec); free(first); free(bid); free(Cb); free(Ab); free(Tk);
     }
     return fail == 0 ? 0 : (fail & 1 ? -1 : -4);
+}
+
+/* Mesh point probe: for m world points, the owner brick (cell rule), the value
+ * from that brick's elements, the chosen element and its smallest barycentric
+ * coordinate. Returns 0, -1/-2 as mesh_index_build, -4 if a point's cell lies in
+ * no brick. */
+int orc_mesh_sample(const orc_scene *sc, int m, const double *pts, double *vals, long long *elem,
+                    double *minb, int *brick)
+{
+    if (!sc || !sc->mesh_tets) return -2;
+    mesh_index mi;
+    int rc = mesh_index_build(sc, &mi);
+    if (rc) return rc;
+    const int nm = nmax3(sc->dims);
+    for (int i = 0; i < m; ++i) {
+        const double *p = pts + 3 * (long long)i;
+        int c[3], b = -1, gap = 0;
+        for (int a = 0; a < 3; ++a) c[a] = clampi((long long)floor(p[a] * nm), 0, sc->dims[a] - 1);
+        for (int j = 0; j < sc->nb; ++j)
+            if (in_box(sc->boxes + 6 * j, c)) { b = j; break; }
+        if (b < 0) { rc = -4; break; }
+        brick[i] = b;
+        vals[i] = sample_mesh(sc, &mi, b, p, &gap, elem + i, minb + i);
+    }
+    mesh_index_free(&mi);
+    return rc;
 }
 
 /* Point probes of the two per-sample stages, for function-level pins. */

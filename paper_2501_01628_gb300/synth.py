@@ -282,3 +282,112 @@ def field_volume_torch(draws: FieldDraws, step: int, n: int, device="cuda", nois
 
 def volume_range(vol: np.ndarray):
     return float(vol.min()), float(vol.max())
+
+
+# --------------------------------------------------------------------------
+# Tetrahedral meshes (unstructured-element workloads). The paper's data set is
+# a mixed finite-element mesh whose parts sit unevenly in space (Sec. 5); these
+# meshes stand in for it: graded, jittered, conforming, each element inside
+# one brick, so that every rank holds whole elements.
+# --------------------------------------------------------------------------
+
+# Kuhn split of a hexahedral cell into six tetrahedra: each follows a monotone
+# corner path 000 -> e_a -> e_a + e_b -> 111 for one axis order (a, b, c). Both
+# sides of a shared face split it along the same diagonal, so neighbouring
+# cells conform.
+_KUHN_ORDERS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def grid_tets(nx: int, ny: int, nz: int) -> np.ndarray:
+    """Six Kuhn tetrahedra per cell of an nx x ny x nz node grid (node index
+    (iz*ny + iy)*nx + ix), int32 (6 (nx-1)(ny-1)(nz-1), 4)."""
+    cx, cy, cz = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), np.arange(nz - 1), indexing="ij")
+    cx, cy, cz = cx.ravel(), cy.ravel(), cz.ravel()
+    tets = []
+    for order in _KUHN_ORDERS:
+        corner = [cx.copy(), cy.copy(), cz.copy()]
+        path = [(corner[2] * ny + corner[1]) * nx + corner[0]]
+        for a in order:
+            corner[a] = corner[a] + 1
+            path.append((corner[2] * ny + corner[1]) * nx + corner[0])
+        tets.append(np.stack(path, axis=1))
+    return np.concatenate(tets, axis=0).astype(np.int32)
+
+
+def _axis_nodes(cuts, cell_voxels: float, focus: float, refine: float, width: float, nmax: int):
+    """Node coordinates (voxel units) along one axis and a flag per node that
+    is a cut. Between consecutive cuts the nodes are uniform, about
+    cell_voxels / (1 + refine * exp(-(x - focus)^2 / (2 width^2))) apart, x the
+    interval's midpoint in world units."""
+    xs, fixed = [float(cuts[0])], [True]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        mid = 0.5 * (a + b) / nmax
+        h = cell_voxels / (1.0 + refine * math.exp(-((mid - focus) ** 2) / (2.0 * width * width)))
+        m = max(1, int(round((b - a) / h)))
+        xs.extend(a + (b - a) * np.arange(1, m) / m)
+        xs.append(float(b))
+        fixed.extend([False] * (m - 1) + [True])
+    return np.asarray(xs, dtype=np.float64), np.asarray(fixed, dtype=bool)
+
+
+def tet_mesh(dims, boxes, rng: np.random.Generator, cell_voxels: float = 4.0, jitter: float = 0.15,
+             focus=(0.5, 0.5, 0.5), refine: float = 0.0, width: float = 0.15):
+    """Conforming tetrahedral mesh of the domain [0, dims/Nmax] in which every
+    element lies inside one half-open brick box of `boxes` (voxel units).
+
+    Per axis, every brick boundary is a node plane and the nodes between two
+    consecutive boundaries are uniform (see _axis_nodes: graded towards
+    `focus` when refine > 0, so bricks hold very different element counts).
+    Each cell of the node grid is split into six tetrahedra (Kuhn). Nodes off a
+    boundary plane are moved along that axis by U[-1, 1] * jitter * (the
+    smaller adjacent spacing). Draws, in order: nv*3 U[-1, 1] (nodes x fastest,
+    then y, then z; xyz per node).
+
+    Returns (verts float32 (nv, 3) world units, tets int32 (nt, 4)), every
+    element positively oriented."""
+    dims = [int(d) for d in dims]
+    nmax = max(dims)
+    boxes = np.asarray(boxes, dtype=np.int64).reshape(-1, 6)
+    nodes, fixed, gaps = [], [], []
+    for a in range(3):
+        cuts = np.unique(np.concatenate([boxes[:, a], boxes[:, 3 + a], [0, dims[a]]]))
+        x, f = _axis_nodes(cuts, cell_voxels, focus[a], refine, width, nmax)
+        d = np.diff(x)
+        g = np.minimum(np.concatenate([[np.inf], d]), np.concatenate([d, [np.inf]]))
+        nodes.append(x)
+        fixed.append(f)
+        gaps.append(g)
+    nx, ny, nz = (len(x) for x in nodes)
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    idx = [xx.ravel(), yy.ravel(), zz.ravel()]
+    u = rng.uniform(-1.0, 1.0, size=(idx[0].size, 3))
+    verts = np.empty((idx[0].size, 3), dtype=np.float64)
+    for a in range(3):
+        i = idx[a]
+        move = np.where(fixed[a][i], 0.0, jitter * np.where(np.isfinite(gaps[a][i]), gaps[a][i], 0.0))
+        verts[:, a] = (nodes[a][i] + u[:, a] * move) / nmax
+    tets = grid_tets(nx, ny, nz)
+    v32 = verts.astype(np.float32)
+    p = v32.astype(np.float64)[tets]
+    vol = np.einsum("ij,ij->i", p[:, 1] - p[:, 0], np.cross(p[:, 2] - p[:, 0], p[:, 3] - p[:, 0]))
+    flip = vol < 0
+    tets[flip] = tets[flip][:, [0, 2, 1, 3]]
+    if not np.all(np.abs(vol) > 0):
+        raise ValueError("degenerate element; lower the jitter")
+    return v32, tets
+
+
+def mesh_field(rng: np.random.Generator, verts: np.ndarray, n_blobs: int = 12, n_waves: int = 8):
+    """Vertex values: blobs (draw_blobs) plus 0.1 * mean of n_waves sinusoids
+    sin(k . p + phi), min-max normalised to [0, 1]. Draws, in order: the blobs,
+    n_waves*3 wave numbers N(0, 12), n_waves phases U[0, 2 pi]."""
+    blobs = draw_blobs(rng, n_blobs)
+    k = rng.normal(0.0, 12.0, size=(n_waves, 3))
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=n_waves)
+    p = verts.astype(np.float64)
+    val = np.zeros(p.shape[0])
+    for c, s, a in zip(blobs.centers, blobs.sigmas, blobs.amps):
+        val += a * np.exp(-np.sum((p - c) ** 2, axis=1) / (2.0 * s * s))
+    val += 0.1 * np.mean(np.sin(p @ k.T + phi), axis=1)
+    val = (val - val.min()) / (val.max() - val.min())
+    return val.astype(np.float32)
