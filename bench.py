@@ -47,7 +47,7 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="paper",
-                    choices=["paper", "small", "precision", "grad", "batch", "stream"])
+                    choices=["paper", "small", "precision", "grad", "batch", "stream", "mesh"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -760,8 +760,154 @@ def run_stream(a):
     print(json.dumps(line))
 
 
+MESH_NAME = ("unstructured elements: 25.0M-tetrahedron graded jittered mesh of a 512^3 nominal domain "
+             "(seed 5; 0.20M..2.60M elements per brick), 36 bricks (4x3x3), 1920x1080 perspective 60 deg "
+             "orbit (8 views), step 0.5 voxel, early termination at alpha 0.99, radix-k composite 4x3x3")
+
+
+def mesh_oracle_rate(verts, vals, tets, boxes, tf, cams, step, ert, n_pix: int = 3000):
+    """Oracle samples/s on n_pix pixels spread over one view (one call: the
+    oracle builds its element index, then renders the pixels; both timed)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    cam = cams[1]
+    W, H = cam["width"], cam["height"]
+    rng = np.random.default_rng(9)
+    pix = np.stack([rng.integers(0, W, n_pix), rng.integers(0, H, n_pix)], axis=1)
+    mesh = oracle.Mesh(verts, vals, tets, (512, 512, 512))
+    t = time.perf_counter()
+    r = oracle.render(mesh, boxes, tf, 0.0, 1.0, cam, step, ert, pixels=pix, threads=cores)
+    dt = time.perf_counter() - t
+    return dict(value=r["nsamples"] / dt, unit=UNIT, cores=cores, kind="oracle",
+                sample="%d random pixels of one 1920x1080 view (%d samples, %.1f s incl. the oracle's element "
+                       "index build, FP64, %d threads)" % (n_pix, r["nsamples"], dt, cores)), r["nsamples"], dt
+
+
+def run_mesh(a):
+    """Tetrahedral-mesh volumes (the paper's data set is an unevenly distributed
+    mixed-element mesh, Sec. 5): one step = one composited frame of the next
+    orbit view; per-brick BVH point location + face-neighbour walk, then the
+    sort-last composite."""
+    import numpy as np
+    from paper_2501_01628_gb300 import synth
+    verts, vals, tets, tf, boxes = synth.mesh_scene()
+    cams = [synth.orbit_camera(1920, 1080, az) for az in synth.ORBIT_AZIMUTHS]
+    step, ert = 0.5, 0.99
+    if a.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        cpu, n, dt = mesh_oracle_rate(verts, vals, tets, boxes, tf, cams, step, ert, n_pix=1500)
+        line = dict(impl="reference", metric=METRIC, value=cpu["value"], unit=UNIT, n_gpus=0, steps=1, warmup=0,
+                    ms_per_step=dt * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                    data="synthetic", config=dict(workload=MESH_NAME, sample=cpu["sample"]), cpu_baseline=cpu,
+                    e2e=dict(value=cpu["value"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+        print(json.dumps(line))
+        return
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_01628_gb300 import vr
+    part = dict(kind="grid", grid=(4, 3, 3))
+    ctx = vr.vr_create(0)
+    t0 = time.perf_counter()
+    m = vr.vr_mesh_create(ctx, verts, vals, tets, (512, 512, 512), part)
+    create_s = time.perf_counter() - t0
+    per_brick, mesh_bytes = vr.vr_mesh_info(m)
+    vr.vr_set_transfer_function(ctx, tf, 0.0, 1.0)
+    vr.vr_set_render_params(ctx, step, ert)
+    vr.vr_set_composite_schedule(ctx, (4, 3, 3))
+    W, H = 1920, 1080
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    counts = []
+    vr.vr_set_count_samples(ctx, True)
+    for cam in cams:
+        vr.vr_set_camera(ctx, cam)
+        vr.vr_render_mesh_frame(ctx, m, out)
+        counts.append(vr.vr_get_sample_count(ctx))
+    vr.vr_set_count_samples(ctx, False)
+    views = [i % len(cams) for i in range(a.warmup + a.steps)]
+    for i in range(a.warmup):
+        vr.vr_set_camera(ctx, cams[views[i]])
+        vr.vr_render_mesh_frame(ctx, m, out)
+    vr.vr_sync(ctx)
+    timed_views = views[a.warmup:]
+    clocks = ClockSampler(0)
+    clocks.start()
+    vr.vr_get_kernel_timing(ctx)
+    vr.vr_set_kernel_timing(ctx, True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for vi in timed_views:
+        vr.vr_set_camera(ctx, cams[vi])
+        vr.vr_render_mesh_frame(ctx, m, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    kt = vr.vr_get_kernel_timing(ctx)
+    vr.vr_set_kernel_timing(ctx, False)
+    hosts = [torch.empty((H, W, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
+    vr.vr_set_host_output_async(ctx, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, vi in enumerate(timed_views):
+        vr.vr_set_camera(ctx, cams[vi])
+        vr.vr_render_mesh_frame(ctx, m, hosts[i & 1])
+    vr.vr_sync(ctx)
+    e2e_s = time.perf_counter() - t0
+    vr.vr_set_host_output_async(ctx, False)
+    vr.vr_mesh_release(m)
+    vr.vr_destroy(ctx)
+    K = a.steps
+    samples = float(sum(counts[vi] for vi in timed_views))
+    march_ms = kt["march_ms"] / max(1, kt["march_launches"])
+    comp_ms = kt["composite_ms"] / max(1, kt["composite_launches"])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm_src = "of measured" if peaks.get("hbm_gbs") else "of fallback"
+    # compulsory bytes of one march: every element record, neighbour entry and
+    # BVH node read at most once (upper bound: the whole mesh) + partial writes
+    rects_sum = 0
+    for vi in timed_views[:len(cams)]:
+        _, rects = vr.vr_plan_view((512, 512, 512), part, cams[vi])
+        rects_sum += int(sum(int(r[2]) * int(r[3]) for r in rects))
+    mean_rect = rects_sum / min(len(cams), len(timed_views))
+    march_bytes = mesh_bytes + mean_rect * 16
+    march_gbs = march_bytes / (march_ms / 1e3) / 1e9
+    cpu = None
+    if not a.no_cpu_baseline:
+        cpu, _, _ = mesh_oracle_rate(verts, vals, tets, boxes, tf, cams, step, ert)
+    line = dict(
+        metric=METRIC, value=samples / (ms / 1e3), unit=UNIT, n_gpus=1, steps=K, warmup=a.warmup,
+        ms_per_step=ms / K, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic",
+        config=dict(workload=MESH_NAME, elements=int(tets.shape[0]), vertices=int(verts.shape[0]),
+                    elements_per_brick=[int(min(per_brick)), int(max(per_brick))], bricks=36, image=[W, H],
+                    views=len(cams), l2="inputs larger than L2: %.2f GB of mesh records vs 129 MB L2"
+                    % (mesh_bytes / 1e9), parallelism="1 GPU"),
+        frames_per_s=K / (ms / 1e3), samples_per_frame=samples / K, gpu_launches=2 * K, clocks=clk,
+        roofline=dict(bound="hbm", kernel="march_mesh", achieved=march_gbs, peak=hbm, unit="GB/s",
+                      frac=march_gbs / hbm, traffic=None,
+                      note="upper-bound compulsory bytes (whole mesh once + partial writes) / mean march "
+                           "launch, %s; the walk is latency-bound (dependent element loads)" % hbm_src),
+        kernel_ms=dict(march=march_ms, composite=comp_ms), mesh_create_s=create_s, mesh_device_bytes=mesh_bytes,
+        cpu_baseline=cpu,
+        e2e=dict(value=samples / e2e_s, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=W * H * 16,
+                 note="vr_render_mesh_frame into pinned host memory (asynchronous double-buffered copies), "
+                      "all frames waited for"))
+    print(json.dumps(line))
+
+
 def main():
     a = args_parse()
+    if a.workload == "mesh":
+        run_mesh(a)
+        return
     if a.workload == "stream":
         run_stream(a)
         return

@@ -53,6 +53,7 @@ typedef struct vr_ctx_s *vr_ctx;
 typedef struct vr_volume_s *vr_volume;
 typedef struct vr_frame_s *vr_frame;
 typedef struct vr_batch_s *vr_batch;
+typedef struct vr_mesh_s *vr_mesh;
 
 typedef enum {
     VR_OK = 0,
@@ -298,6 +299,47 @@ vr_status vr_volume_update_async(vr_volume vol, const float *src, int src_on_dev
  * between runs. */
 vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_dev, float *grad_tf_dev,
                              float *grad_density_dev, void *stream);
+
+/* ---- unstructured elements (tetrahedral meshes) ------------------------- */
+
+/* Sec. 5: the paper renders a mixed finite-element data set kept in the
+ * distribution its simulation used, each rank holding whole elements, unevenly
+ * spread in space; Sec. 2.1: rays find the objects they meet through a bounding
+ * volume hierarchy. Here the elements are tetrahedra (a mixed mesh enters as its
+ * tetrahedral decomposition) and the ranks are the bricks of `part`.
+ *
+ * Create a mesh volume from HOST arrays (copied; the library owns the result
+ * until vr_mesh_release):
+ *   verts   n_verts x 3 float32 world positions inside [0, dims/Nmax];
+ *   values  n_verts float32 vertex values;
+ *   tets    n_tets x 4 int32 vertex indices (either orientation).
+ * `dims` is the nominal lattice: as for a voxel volume it fixes the domain box,
+ * the sample spacing (step_voxels / Nmax) and the sample ownership cells. Each
+ * element belongs to the brick whose box holds its centroid's cell and must lie
+ * inside that box (1e-3 voxel tolerance); each brick's elements must fill its box
+ * without gaps or overlaps (volumes checked to 1e-4) and share faces only
+ * pairwise. A violation, a degenerate element or an empty brick gives
+ * VR_ERR_ARG. The per-brick BVHs and face adjacency are built on the host.
+ *
+ * Sampling (reading; the paper gives none): a lattice sample keeps the owner of
+ * the voxel path (its cell's brick) and takes the linear interpolant
+ * sum_i lambda_i s_i of the owner's element containing it; rendering,
+ * classification, early termination, opacity correction and compositing are
+ * those of vr_render_frame (sort-last mode only). Device memory: 80 bytes per
+ * element (record + neighbours) plus 32 bytes per BVH node. */
+vr_status vr_mesh_create(vr_ctx ctx, const int dims[3], const vr_partition *part, const float *verts,
+                         long long n_verts, const float *values, const int *tets, long long n_tets,
+                         vr_mesh *out);
+vr_status vr_mesh_release(vr_mesh mesh);
+/* Number of bricks, elements per brick (n long longs, may be NULL) and device
+ * bytes of the mesh (may be NULL). */
+vr_status vr_mesh_info(vr_mesh mesh, int *n_bricks, long long *elements_per_brick, long long *device_bytes);
+/* One frame of the mesh with the context's camera, transfer function and
+ * parameters: per-brick partials (BVH point location of each ray's first owned
+ * sample, then a walk through face neighbours), then the composite, into
+ * out_rgba (H x W x 4 float32; device if out_on_device, else host). Asynchronous
+ * on `stream` like vr_render_frame. VR_ERR_STATE in ray-state cycling mode. */
+vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int out_on_device, void *stream);
 
 /* ---- rendering without device allocation -------------------------------- */
 

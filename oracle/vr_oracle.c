@@ -154,7 +154,8 @@ static double sample_trilinear(const orc_scene *sc, const double p[3])
  *     min_i lambda_i(p), the barycentric coordinates of p. For p inside an
  *     element that is the element; on a shared face every candidate gives the
  *     same value (the interpolant is continuous on a conforming mesh); p
- *     outside every element by rounding takes the nearest one.
+ *     outside every element by rounding, or outside the domain box, takes the
+ *     nearest one.
  * Barycentrics by Cramer's rule on the edge matrix [v1-v0, v2-v0, v3-v0]. */
 static void cross3(const double a[3], const double b[3], double o[3]);
 
@@ -324,8 +325,13 @@ static double sample_mesh(const orc_scene *sc, const mesh_index *mi, int brick, 
         }
     }
     /* float32 vertices on a brick plane lo/Nmax that is not a binary fraction
-     * sit up to ~1e-7 of an element off the plane; a real hole is far larger */
-    if (!(best >= -1e-5)) *gap = 1;
+     * sit up to ~1e-7 of an element off the plane; a real hole is far larger.
+     * Outside the domain box (the ambiguity probes take samples up to a few
+     * 1e-6 past t_out) the nearest element extends the field, as clamp-to-edge
+     * does for voxels. */
+    const int inside = p[0] >= 0.0 && p[0] <= mi->E[0] && p[1] >= 0.0 && p[1] <= mi->E[1] && p[2] >= 0.0 &&
+                       p[2] <= mi->E[2];
+    if (!(best >= -1e-5) && inside) *gap = 1;
     if (elem) *elem = be;
     if (minb) *minb = best;
     return val;

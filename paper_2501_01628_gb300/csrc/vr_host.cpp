@@ -768,6 +768,7 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
     if (err) {
         VR_CUDA(ctx, cudaMemset(ctx->d_error, 0, sizeof(int)));
         if (err & 2) return fail(ctx, VR_ERR_TIMEOUT, "a bounded device-side wait of the batched kernel gave up");
+        if (err & 8) return fail(ctx, VR_ERR_BOUNDS, "a mesh point location found no element");
         return fail(ctx, VR_ERR_BOUNDS, "a backward pass met an owned-sample run longer than 4096 samples");
     }
     return VR_OK;

@@ -1,0 +1,219 @@
+// vr_mesh.cu -- march kernel (sm_103a) of tetrahedral-mesh volumes: the same
+// per-brick emission-absorption runs on the global lattice as the voxel march
+// (Sec. 2.2: each rank renders the samples of its share of the data), with the
+// value taken from the brick's elements instead of a voxel grid.
+//
+// Per pixel and brick: the owned run [ka, kb] of lattice samples (ownership by
+// the sample's cell, exactly as for voxel bricks), the element containing the
+// first sample from a BVH point query, then a walk through face neighbours. In
+// an element the value is linear in t and the ray leaves through the face whose
+// barycentric coordinate falls to 0 first; every sample with t up to that exit
+// parameter is classified and accumulated from the element's plane equation.
+#include "vr_device.cuh"
+#include "vr_mesh.h"
+
+namespace vr {
+namespace {
+
+using dev::find_brick;
+
+struct Elem {
+    float cx, cy, cz, s0;       // centroid, value at the centroid
+    float gx, gy, gz;           // value gradient
+    float n[4][3];              // barycentric gradients, faces 0..3
+};
+
+__device__ __forceinline__ void load_elem(const float4 *rec, Elem &E)
+{
+    const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2), r3 = __ldg(rec + 3);
+    E.cx = r0.x;
+    E.cy = r0.y;
+    E.cz = r0.z;
+    E.s0 = r0.w;
+    E.n[1][0] = r1.x; E.n[1][1] = r1.y; E.n[1][2] = r1.z;
+    E.n[2][0] = r2.x; E.n[2][1] = r2.y; E.n[2][2] = r2.z;
+    E.n[3][0] = r3.x; E.n[3][1] = r3.y; E.n[3][2] = r3.z;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) E.n[0][a] = -(E.n[1][a] + E.n[2][a] + E.n[3][a]);
+    E.gx = fmaf(r1.w, r1.x, fmaf(r2.w, r2.x, r3.w * r3.x));
+    E.gy = fmaf(r1.w, r1.y, fmaf(r2.w, r2.y, r3.w * r3.y));
+    E.gz = fmaf(r1.w, r1.z, fmaf(r2.w, r2.z, r3.w * r3.z));
+}
+
+// Smallest barycentric coordinate of q in the element (record at rec).
+__device__ __forceinline__ float min_bary(const float4 *rec, float qx, float qy, float qz)
+{
+    const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2), r3 = __ldg(rec + 3);
+    const float dx = qx - r0.x, dy = qy - r0.y, dz = qz - r0.z;
+    const float l1 = fmaf(r1.x, dx, fmaf(r1.y, dy, fmaf(r1.z, dz, 0.25f)));
+    const float l2 = fmaf(r2.x, dx, fmaf(r2.y, dy, fmaf(r2.z, dz, 0.25f)));
+    const float l3 = fmaf(r3.x, dx, fmaf(r3.y, dy, fmaf(r3.z, dz, 0.25f)));
+    const float l0 = 1.0f - l1 - l2 - l3;
+    return fminf(fminf(l0, l1), fminf(l2, l3));
+}
+
+// Brick-local element containing q (largest smallest-barycentric among the
+// leaves whose boxes hold q; the search stops at the first element holding q).
+// Returns -1 only when no leaf box holds q.
+__device__ int locate(const MeshParams &p, int brick, float qx, float qy, float qz)
+{
+    const MeshNode *nodes = p.nodes + p.node_base[brick];
+    const float4 *rec = p.rec + kMeshRec * p.rec_base[brick];
+    int stack[kMeshStack];
+    int sp = 0, node = 0, best = -1;
+    float best_m = -3.0e38f;
+    constexpr float eps = 1.0e-3f;  // voxel units
+    while (true) {
+        const MeshNode nd = nodes[node];
+        const bool in = qx >= nd.lo[0] - eps && qx <= nd.hi[0] + eps && qy >= nd.lo[1] - eps &&
+                        qy <= nd.hi[1] + eps && qz >= nd.lo[2] - eps && qz <= nd.hi[2] + eps;
+        if (in) {
+            if (nd.count == 0) {
+                if (sp < kMeshStack) stack[sp++] = nd.first + 1;
+                node = nd.first;
+                continue;
+            }
+            for (int i = 0; i < nd.count; ++i) {
+                const int e = nd.first + i;
+                const float m = min_bary(rec + kMeshRec * e, qx, qy, qz);
+                if (m > best_m) {
+                    best_m = m;
+                    best = e;
+                }
+            }
+            if (best_m >= 0.0f) return best;
+        }
+        if (sp == 0) return best;
+        node = stack[--sp];
+    }
+}
+
+template <bool COUNT, bool OPC>
+__global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__ MeshParams P)
+{
+    const MarchParams &p = P.m;
+    const int item = blockIdx.x;
+    const int bi = find_brick(p, item);
+    const BrickLaunch &B = p.b[bi];
+    const int local = item - B.item_begin;
+    const int ty = local / B.tiles_x, tx = local - ty * B.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rx = tx * p.tile_w + (warp & 1) * p.pw + (lane & (p.pw - 1));
+    const int ry = ty * p.tile_h + (warp >> 1) * (32 / p.pw) + lane / p.pw;
+    if (rx >= B.rect[2] || ry >= B.rect[3]) return;
+    const int px = B.rect[0] + rx, py = B.rect[1] + ry;
+
+    dev::Ray ray;
+    dev::ray_setup(p, px, py, ray);
+    dev::OwnedRun run;
+    dev::brick_run(p, B, ray, run);
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+    unsigned long long executed = 0;
+    if (run.ka <= run.kb) {
+        const float4 *rec = P.rec + kMeshRec * P.rec_base[bi];
+        const int4 *nbr = P.nbr + P.rec_base[bi];
+        const float4 *tf = p.tf;
+        const float xmax = static_cast<float>(p.ntf - 1);
+        const float dvx = ray.dv[0], dvy = ray.dv[1], dvz = ray.dv[2];
+        int k = run.ka;
+        float t = fmaf(static_cast<float>(k) + 0.5f, p.dt, ray.t_in);
+        float qx = fmaf(t, dvx, ray.ov[0]), qy = fmaf(t, dvy, ray.ov[1]), qz = fmaf(t, dvz, ray.ov[2]);
+        int e = locate(P, bi, qx, qy, qz);
+        if (e < 0) {
+            atomicOr(P.error, 8);
+            e = 0;
+        }
+        bool forced = true;  // a located element takes its first sample unconditionally
+        int stall = 0;
+        Elem E;
+        float t_exit = 0.f;
+        int face = -1;
+        bool fresh = true;
+        while (true) {
+            if (fresh) {
+                load_elem(rec + kMeshRec * e, E);
+                // exit parameter: smallest t > current at which a decreasing
+                // barycentric coordinate reaches 0, measured from the current
+                // sample position
+                const float dx = qx - E.cx, dy = qy - E.cy, dz = qz - E.cz;
+                t_exit = 3.0e38f;
+                face = -1;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const float beta = fmaf(E.n[f][0], dvx, fmaf(E.n[f][1], dvy, E.n[f][2] * dvz));
+                    const float lam = fmaf(E.n[f][0], dx, fmaf(E.n[f][1], dy, fmaf(E.n[f][2], dz, 0.25f)));
+                    if (beta < 0.0f) {
+                        const float tf_ = t - __fdividef(lam, beta);
+                        if (tf_ < t_exit) {
+                            t_exit = tf_;
+                            face = f;
+                        }
+                    }
+                }
+                fresh = false;
+            }
+            if (forced || t <= t_exit) {
+                forced = false;
+                stall = 0;
+                const float s = fmaf(E.gx, qx - E.cx, fmaf(E.gy, qy - E.cy, fmaf(E.gz, qz - E.cz, E.s0)));
+                const float x = fminf(fmaxf(fmaf(s, p.tf_scale, p.tf_bias), 0.0f), xmax);
+                const int ti = static_cast<int>(x);
+                const float w = x - static_cast<float>(ti);
+                const float4 e0 = __ldg(tf + 2 * ti), de = __ldg(tf + 2 * ti + 1);
+                float al = fmaf(w, de.w, e0.w);
+                if (OPC) al = -expm1f(p.opc_ratio * log1pf(-al));
+                const float ta = T * al;
+                C0 = fmaf(ta, fmaf(w, de.x, e0.x), C0);
+                C1 = fmaf(ta, fmaf(w, de.y, e0.y), C1);
+                C2 = fmaf(ta, fmaf(w, de.z, e0.z), C2);
+                T = T - ta;
+                if (COUNT) ++executed;
+                if (T <= p.ert_T || k >= run.kb) break;
+                ++k;
+                t = fmaf(static_cast<float>(k) + 0.5f, p.dt, ray.t_in);
+                qx = fmaf(t, dvx, ray.ov[0]);
+                qy = fmaf(t, dvy, ray.ov[1]);
+                qz = fmaf(t, dvz, ray.ov[2]);
+                continue;
+            }
+            // the next sample lies beyond this element: step to the neighbour
+            // across the exit face, or locate again after a boundary face or
+            // too many steps without a sample (rounding near edges/vertices)
+            int nx = -1;
+            if (face >= 0) {
+                const int4 nb = __ldg(nbr + e);
+                nx = face == 0 ? nb.x : face == 1 ? nb.y : face == 2 ? nb.z : nb.w;
+            }
+            if (nx < 0 || ++stall > kMeshStallSteps) {
+                nx = locate(P, bi, qx, qy, qz);
+                if (nx < 0) {
+                    atomicOr(P.error, 8);
+                    nx = e;
+                }
+                forced = true;
+            }
+            e = nx;
+            fresh = true;
+        }
+    }
+    p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = make_float4(C0, C1, C2, 1.0f - T);
+    if (COUNT && executed) atomicAdd(p.sample_counter, executed);
+}
+
+}  // namespace
+
+cudaError_t launch_march_mesh(const MeshParams &p, cudaStream_t s)
+{
+    if (p.m.n_items <= 0) return cudaSuccess;
+    const bool count = p.m.sample_counter != nullptr, opc = p.m.opc_ratio != 1.0f;
+    if (count) {
+        if (opc) march_mesh_kernel<true, true><<<p.m.n_items, 128, 0, s>>>(p);
+        else march_mesh_kernel<true, false><<<p.m.n_items, 128, 0, s>>>(p);
+    } else {
+        if (opc) march_mesh_kernel<false, true><<<p.m.n_items, 128, 0, s>>>(p);
+        else march_mesh_kernel<false, false><<<p.m.n_items, 128, 0, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vr

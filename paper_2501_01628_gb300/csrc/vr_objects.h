@@ -119,6 +119,15 @@ struct Basis {
 };
 bool make_basis(const vr_camera &c, Basis &B);
 void footprint(const vr_camera &c, const Basis &B, const int box[6], double nmax, int rect[4]);
+bool partition_plan(const int dims[3], const vr_partition *part, std::vector<int> &boxes,
+                    std::vector<KdNode> &tree, const char **why);
+// Per-view setup of a partitioned object (visibility order, footprints, launch
+// table); reads only the geometry fields of `vol` (dims, boxes, tree, base, d_data).
+vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &mp);
+vr_status ensure_frame(vr_ctx ctx, vr_frame_s &fr, long long px);
+vr_status composite_to(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s);
+int timing_begin(vr_ctx ctx, int kind, cudaStream_t s);
+void timing_end(vr_ctx ctx, int idx, cudaStream_t s);
 
 }  // namespace host
 }  // namespace vr

@@ -391,3 +391,28 @@ def mesh_field(rng: np.random.Generator, verts: np.ndarray, n_blobs: int = 12, n
     val += 0.1 * np.mean(np.sin(p @ k.T + phi), axis=1)
     val = (val - val.min()) / (val.max() - val.min())
     return val.astype(np.float32)
+
+
+def mesh_scene(n: int = 512, seed: int = 5, grid=(4, 3, 3), cell_voxels: float = 5.0, refine: float = 1.5,
+               focus=(0.35, 0.55, 0.45)):
+    """Unstructured-element workload: a graded, jittered tetrahedral mesh of the
+    n^3 nominal domain conforming to a grid of bricks (element density up to
+    (1 + refine)^3 times higher near `focus`, so bricks hold very different
+    element counts), vertex values from mesh_field, then a random TF. Draws, in
+    order (default_rng(seed)): tet_mesh's jitter, mesh_field, random_tf.
+    Returns (verts, vals, tets, tf, boxes)."""
+    rng = np.random.default_rng(seed)
+    gx, gy, gz = grid
+    boxes = []
+    for bz in range(gz):
+        for by in range(gy):
+            for bx in range(gx):
+                b = (bx, by, bz)
+                g = (gx, gy, gz)
+                boxes.append([n * b[a] // g[a] for a in range(3)] + [n * (b[a] + 1) // g[a] for a in range(3)])
+    boxes = np.asarray(boxes, dtype=np.int32)
+    verts, tets = tet_mesh((n, n, n), boxes, rng, cell_voxels=cell_voxels, jitter=0.2, focus=focus,
+                           refine=refine)
+    vals = mesh_field(rng, verts)
+    tf = random_tf(rng)
+    return verts, vals, tets, tf, boxes

@@ -38,7 +38,8 @@ EXPORTS = (
     "vr_volume_update", "vr_render_backward", "vr_batch_create", "vr_batch_launch",
     "vr_batch_autotune", "vr_batch_release", "vr_batch_configure", "vr_set_render_mode",
     "vr_set_opacity_correction", "vr_volume_update_async", "vr_set_packet_width",
-    "vr_set_host_output_async",
+    "vr_set_host_output_async", "vr_mesh_create", "vr_mesh_release", "vr_mesh_info",
+    "vr_render_mesh_frame",
 )
 
 
@@ -104,6 +105,11 @@ _SIG = {
     "vr_render_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
     "vr_plan_view": (_I, [_P, ctypes.POINTER(vr_partition), ctypes.POINTER(vr_camera), _P, _P]),
+    "vr_mesh_create": (_I, [_P, _P, ctypes.POINTER(vr_partition), _P, ctypes.c_longlong, _P, _P,
+                            ctypes.c_longlong, ctypes.POINTER(_P)]),
+    "vr_mesh_release": (_I, [_P]),
+    "vr_mesh_info": (_I, [_P, _P, _P, _P]),
+    "vr_render_mesh_frame": (_I, [_P, _P, _P, _I, _P]),
 }
 
 
@@ -450,6 +456,42 @@ def vr_frame_release(frame):
 def vr_render_frame(ctx, vol, out, stream=None):
     ptr, on_dev, _ = _ptr_and_loc(out)
     _check(lib().vr_render_frame(ctx, vol, ptr, on_dev, _stream(stream)), ctx, "vr_render_frame")
+
+
+def vr_mesh_create(ctx, verts, values, tets, dims, partition=None):
+    """Tetrahedral-mesh volume from host arrays: verts (nv, 3) float32 world
+    positions, values (nv,) float32, tets (nt, 4) int32; dims the nominal
+    lattice (Nx, Ny, Nz); partition as for vr_volume_create."""
+    v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+    s = np.ascontiguousarray(values, dtype=np.float32).ravel()
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    if s.size != v.shape[0]:
+        raise ValueError("one value per vertex")
+    d = (ctypes.c_int * 3)(*[int(x) for x in dims])
+    part, keep = make_partition(**(partition or {}))
+    h = ctypes.c_void_p()
+    _check(lib().vr_mesh_create(ctx, d, ctypes.byref(part), v.ctypes.data, v.shape[0], s.ctypes.data,
+                                t.ctypes.data, t.shape[0], ctypes.byref(h)), ctx, "vr_mesh_create")
+    return h
+
+
+def vr_mesh_release(mesh):
+    _check(lib().vr_mesh_release(mesh), None, "vr_mesh_release")
+
+
+def vr_mesh_info(mesh):
+    """(elements per brick (n,) int64, device bytes)."""
+    n = ctypes.c_int()
+    _check(lib().vr_mesh_info(mesh, ctypes.byref(n), None, None), None, "vr_mesh_info")
+    cnt = np.zeros(n.value, np.int64)
+    nbytes = ctypes.c_longlong()
+    _check(lib().vr_mesh_info(mesh, None, cnt.ctypes.data, ctypes.byref(nbytes)), None, "vr_mesh_info")
+    return cnt, int(nbytes.value)
+
+
+def vr_render_mesh_frame(ctx, mesh, out, stream=None):
+    ptr, on_dev, _ = _ptr_and_loc(out)
+    _check(lib().vr_render_mesh_frame(ctx, mesh, ptr, on_dev, _stream(stream)), ctx, "vr_render_mesh_frame")
 
 
 def vr_render_frame_noalloc(volume, partition, tf, vmin: float, vmax: float, cam: dict, out,
