@@ -17,29 +17,6 @@ namespace {
 
 using dev::find_brick;
 
-struct Elem {
-    float cx, cy, cz, s0;       // centroid, value at the centroid
-    float gx, gy, gz;           // value gradient
-    float n[4][3];              // barycentric gradients, faces 0..3
-};
-
-__device__ __forceinline__ void load_elem(const float4 *rec, Elem &E)
-{
-    const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2), r3 = __ldg(rec + 3);
-    E.cx = r0.x;
-    E.cy = r0.y;
-    E.cz = r0.z;
-    E.s0 = r0.w;
-    E.n[1][0] = r1.x; E.n[1][1] = r1.y; E.n[1][2] = r1.z;
-    E.n[2][0] = r2.x; E.n[2][1] = r2.y; E.n[2][2] = r2.z;
-    E.n[3][0] = r3.x; E.n[3][1] = r3.y; E.n[3][2] = r3.z;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) E.n[0][a] = -(E.n[1][a] + E.n[2][a] + E.n[3][a]);
-    E.gx = fmaf(r1.w, r1.x, fmaf(r2.w, r2.x, r3.w * r3.x));
-    E.gy = fmaf(r1.w, r1.y, fmaf(r2.w, r2.y, r3.w * r3.y));
-    E.gz = fmaf(r1.w, r1.z, fmaf(r2.w, r2.z, r3.w * r3.z));
-}
-
 // Smallest barycentric coordinate of q in the element (record at rec).
 __device__ __forceinline__ float min_bary(const float4 *rec, float qx, float qy, float qz)
 {
@@ -52,40 +29,41 @@ __device__ __forceinline__ float min_bary(const float4 *rec, float qx, float qy,
     return fminf(fminf(l0, l1), fminf(l2, l3));
 }
 
-// Brick-local element containing q (largest smallest-barycentric among the
-// leaves whose boxes hold q; the search stops at the first element holding q).
-// Returns -1 only when no leaf box holds q.
+// Brick-local element containing q: a stackless preorder walk of the brick's
+// BVH (node indices only increase), keeping the element with the largest
+// smallest-barycentric among the leaves whose boxes hold q and stopping at the
+// first element that holds q. Returns -1 only when no leaf box holds q.
 __device__ int locate(const MeshParams &p, int brick, float qx, float qy, float qz)
 {
     const MeshNode *nodes = p.nodes + p.node_base[brick];
     const float4 *rec = p.rec + kMeshRec * p.rec_base[brick];
-    int stack[kMeshStack];
-    int sp = 0, node = 0, best = -1;
-    float best_m = -3.0e38f;
     constexpr float eps = 1.0e-3f;  // voxel units
-    while (true) {
+    int best = -1;
+    float best_m = -3.0e38f;
+    const int end = nodes[0].skip;
+    int node = 0;
+    while (node < end) {
         const MeshNode nd = nodes[node];
         const bool in = qx >= nd.lo[0] - eps && qx <= nd.hi[0] + eps && qy >= nd.lo[1] - eps &&
                         qy <= nd.hi[1] + eps && qz >= nd.lo[2] - eps && qz <= nd.hi[2] + eps;
+        if (in && nd.leaf == 0) {
+            ++node;
+            continue;
+        }
         if (in) {
-            if (nd.count == 0) {
-                if (sp < kMeshStack) stack[sp++] = nd.first + 1;
-                node = nd.first;
-                continue;
-            }
-            for (int i = 0; i < nd.count; ++i) {
-                const int e = nd.first + i;
-                const float m = min_bary(rec + kMeshRec * e, qx, qy, qz);
+            const int first = nd.leaf & ((1 << 28) - 1), count = nd.leaf >> 28;
+            for (int i = 0; i < count; ++i) {
+                const float m = min_bary(rec + kMeshRec * (first + i), qx, qy, qz);
                 if (m > best_m) {
                     best_m = m;
-                    best = e;
+                    best = first + i;
                 }
             }
             if (best_m >= 0.0f) return best;
         }
-        if (sp == 0) return best;
-        node = stack[--sp];
+        node = nd.skip;
     }
+    return best;
 }
 
 template <bool COUNT, bool OPC>
@@ -125,37 +103,40 @@ __global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__
         }
         bool forced = true;  // a located element takes its first sample unconditionally
         int stall = 0;
-        Elem E;
-        float t_exit = 0.f;
-        int face = -1;
-        bool fresh = true;
+        // One element per iteration: every lane loads its element (the same
+        // instruction stream for the warp), then takes the element's samples.
         while (true) {
-            if (fresh) {
-                load_elem(rec + kMeshRec * e, E);
-                // exit parameter: smallest t > current at which a decreasing
-                // barycentric coordinate reaches 0, measured from the current
-                // sample position
-                const float dx = qx - E.cx, dy = qy - E.cy, dz = qz - E.cz;
-                t_exit = 3.0e38f;
-                face = -1;
-#pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    const float beta = fmaf(E.n[f][0], dvx, fmaf(E.n[f][1], dvy, E.n[f][2] * dvz));
-                    const float lam = fmaf(E.n[f][0], dx, fmaf(E.n[f][1], dy, fmaf(E.n[f][2], dz, 0.25f)));
-                    if (beta < 0.0f) {
-                        const float tf_ = t - __fdividef(lam, beta);
-                        if (tf_ < t_exit) {
-                            t_exit = tf_;
-                            face = f;
-                        }
-                    }
+            const float4 *r = rec + kMeshRec * e;
+            const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
+            const int4 nb = __ldg(nbr + e);  // needed after the samples: issued early
+            // exit parameter: smallest t at which a decreasing barycentric
+            // coordinate reaches 0, measured from the current sample position
+            const float dx = qx - r0.x, dy = qy - r0.y, dz = qz - r0.z;
+            const float n0x = -(r1.x + r2.x + r3.x), n0y = -(r1.y + r2.y + r3.y), n0z = -(r1.z + r2.z + r3.z);
+            float t_exit = 3.0e38f;
+            int face = -1;
+            auto exit_face = [&](float nx, float ny, float nz, int f) {
+                const float beta = fmaf(nx, dvx, fmaf(ny, dvy, nz * dvz));
+                const float lam = fmaf(nx, dx, fmaf(ny, dy, fmaf(nz, dz, 0.25f)));
+                const float tf_ = t - __fdividef(lam, beta);
+                if (beta < 0.0f && tf_ < t_exit) {
+                    t_exit = tf_;
+                    face = f;
                 }
-                fresh = false;
-            }
-            if (forced || t <= t_exit) {
+            };
+            exit_face(n0x, n0y, n0z, 0);
+            exit_face(r1.x, r1.y, r1.z, 1);
+            exit_face(r2.x, r2.y, r2.z, 2);
+            exit_face(r3.x, r3.y, r3.z, 3);
+            // value gradient g = sum_i (s_i - s_0) n_i; value(q) = s_mean + g . (q - c)
+            const float gx = fmaf(r1.w, r1.x, fmaf(r2.w, r2.x, r3.w * r3.x));
+            const float gy = fmaf(r1.w, r1.y, fmaf(r2.w, r2.y, r3.w * r3.y));
+            const float gz = fmaf(r1.w, r1.z, fmaf(r2.w, r2.z, r3.w * r3.z));
+            bool done = false;
+            while (forced || t <= t_exit) {
                 forced = false;
                 stall = 0;
-                const float s = fmaf(E.gx, qx - E.cx, fmaf(E.gy, qy - E.cy, fmaf(E.gz, qz - E.cz, E.s0)));
+                const float s = fmaf(gx, qx - r0.x, fmaf(gy, qy - r0.y, fmaf(gz, qz - r0.z, r0.w)));
                 const float x = fminf(fmaxf(fmaf(s, p.tf_scale, p.tf_bias), 0.0f), xmax);
                 const int ti = static_cast<int>(x);
                 const float w = x - static_cast<float>(ti);
@@ -168,22 +149,21 @@ __global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__
                 C2 = fmaf(ta, fmaf(w, de.z, e0.z), C2);
                 T = T - ta;
                 if (COUNT) ++executed;
-                if (T <= p.ert_T || k >= run.kb) break;
+                if (T <= p.ert_T || k >= run.kb) {
+                    done = true;
+                    break;
+                }
                 ++k;
                 t = fmaf(static_cast<float>(k) + 0.5f, p.dt, ray.t_in);
                 qx = fmaf(t, dvx, ray.ov[0]);
                 qy = fmaf(t, dvy, ray.ov[1]);
                 qz = fmaf(t, dvz, ray.ov[2]);
-                continue;
             }
-            // the next sample lies beyond this element: step to the neighbour
-            // across the exit face, or locate again after a boundary face or
-            // too many steps without a sample (rounding near edges/vertices)
-            int nx = -1;
-            if (face >= 0) {
-                const int4 nb = __ldg(nbr + e);
-                nx = face == 0 ? nb.x : face == 1 ? nb.y : face == 2 ? nb.z : nb.w;
-            }
+            if (done) break;
+            // the next sample lies beyond this element: the neighbour across the
+            // exit face, or a new point location after a boundary face or too
+            // many steps without a sample (rounding near edges and vertices)
+            int nx = face == 0 ? nb.x : face == 1 ? nb.y : face == 2 ? nb.z : face == 3 ? nb.w : -1;
             if (nx < 0 || ++stall > kMeshStallSteps) {
                 nx = locate(P, bi, qx, qy, qz);
                 if (nx < 0) {
@@ -193,7 +173,6 @@ __global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__
                 forced = true;
             }
             e = nx;
-            fresh = true;
         }
     }
     p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = make_float4(C0, C1, C2, 1.0f - T);

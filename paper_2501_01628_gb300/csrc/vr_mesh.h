@@ -24,18 +24,21 @@ namespace vr {
 // Face i is the face opposite vertex i (lambda_i = 0 on it).
 constexpr int kMeshRec = 4;
 
-// BVH node over a brick's elements (voxel units). Inner node: count = 0 and
-// children at brick-local node indices first, first + 1. Leaf: count elements
-// starting at brick-local element index first.
+// BVH node over a brick's elements (voxel units), nodes in preorder: an inner
+// node's first child is the next node; `skip` is the first node after the
+// node's subtree (the root's skip is the node count), so a point query needs no
+// stack. leaf = 0 for an inner node, else (count << 28) | first: count elements
+// from brick-local element index first.
 struct MeshNode {
     float lo[3];
-    int first;
+    int skip;
     float hi[3];
-    int count;
+    int leaf;
 };
 
-constexpr int kMeshStack = 48;        // BVH depth limit (the builder enforces it)
-constexpr int kMeshStallSteps = 32;   // element steps without a sample before re-locating
+constexpr int kMeshLeafMax = 4;        // elements per leaf
+constexpr int kMeshMaxElems = 1 << 28; // elements per brick (leaf encoding)
+constexpr int kMeshStallSteps = 32;    // element steps without a sample before re-locating
 
 struct MeshParams {
     MarchParams m;                    // camera, lattice, transfer function, tiles, bricks

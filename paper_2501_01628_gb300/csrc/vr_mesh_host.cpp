@@ -37,8 +37,6 @@ struct vr_mesh_s {
 
 namespace {
 
-constexpr int kLeafSize = 4;
-
 struct BrickBuild {
     std::vector<long long> elems;   // global element ids in BVH leaf order
     std::vector<MeshNode> nodes;
@@ -63,14 +61,62 @@ inline void vtx(const MeshInput &in, long long e, int j, double v[3])
 }
 
 // Median-split BVH over the brick's elements (centroids along the longest axis
-// of their bounds); reorders b.elems into leaf order. Children follow their
-// parent in the node array, so a point query always moves to higher indices.
+// of their bounds), nodes in preorder with skip links (see vr_mesh.h);
+// reorders b.elems into leaf order.
+struct BvhBuilder {
+    std::vector<std::array<float, 9>> box;  // per element: lo xyz, hi xyz, centroid xyz
+    std::vector<long long> idx;
+    std::vector<MeshNode> *nodes;
+
+    void build(long long begin, long long end)
+    {
+        const int me = static_cast<int>(nodes->size());
+        nodes->push_back(MeshNode{});
+        MeshNode nd{};
+        float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int a = 0; a < 3; ++a) {
+            nd.lo[a] = INFINITY;
+            nd.hi[a] = -INFINITY;
+        }
+        for (long long i = begin; i < end; ++i) {
+            const auto &bx = box[idx[i]];
+            for (int a = 0; a < 3; ++a) {
+                nd.lo[a] = std::min(nd.lo[a], bx[a]);
+                nd.hi[a] = std::max(nd.hi[a], bx[3 + a]);
+                clo[a] = std::min(clo[a], bx[6 + a]);
+                chi[a] = std::max(chi[a], bx[6 + a]);
+            }
+        }
+        const long long cnt = end - begin;
+        if (cnt <= kMeshLeafMax) {
+            nd.leaf = static_cast<int>((cnt << 28) | begin);
+        } else {
+            int axis = 0;
+            for (int a = 1; a < 3; ++a)
+                if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+            const long long mid = begin + cnt / 2;
+            std::nth_element(idx.begin() + begin, idx.begin() + mid, idx.begin() + end,
+                             [&](long long x, long long y) { return box[x][6 + axis] < box[y][6 + axis]; });
+            build(begin, mid);  // depth log2(n / 4): recursion stays shallow
+            build(mid, end);
+            nd.leaf = 0;
+        }
+        nd.skip = static_cast<int>(nodes->size());
+        (*nodes)[me] = nd;
+    }
+};
+
 bool build_bvh(const MeshInput &in, BrickBuild &b)
 {
     const long long n = static_cast<long long>(b.elems.size());
-    std::vector<std::array<float, 9>> box(n);  // lo xyz, hi xyz, centroid xyz
+    if (n >= kMeshMaxElems) {
+        b.err = "too many elements in one brick";
+        return false;
+    }
+    BvhBuilder B;
+    B.box.resize(n);
     for (long long i = 0; i < n; ++i) {
-        auto &bx = box[i];
+        auto &bx = B.box[i];
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, c[3] = {0, 0, 0};
         for (int j = 0; j < 4; ++j) {
             double v[3];
@@ -87,61 +133,14 @@ bool build_bvh(const MeshInput &in, BrickBuild &b)
             bx[6 + a] = static_cast<float>(c[a]);
         }
     }
-    std::vector<long long> idx(n);
-    for (long long i = 0; i < n; ++i) idx[i] = i;
-    struct Work {
-        int node;
-        long long begin, end;
-        int depth;
-    };
+    B.idx.resize(n);
+    for (long long i = 0; i < n; ++i) B.idx[i] = i;
     b.nodes.clear();
-    b.nodes.push_back(MeshNode{});
-    std::vector<Work> stack{{0, 0, n, 1}};
-    while (!stack.empty()) {
-        const Work w = stack.back();
-        stack.pop_back();
-        MeshNode nd{};
-        float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int a = 0; a < 3; ++a) {
-            nd.lo[a] = INFINITY;
-            nd.hi[a] = -INFINITY;
-        }
-        for (long long i = w.begin; i < w.end; ++i) {
-            const auto &bx = box[idx[i]];
-            for (int a = 0; a < 3; ++a) {
-                nd.lo[a] = std::min(nd.lo[a], bx[a]);
-                nd.hi[a] = std::max(nd.hi[a], bx[3 + a]);
-                clo[a] = std::min(clo[a], bx[6 + a]);
-                chi[a] = std::max(chi[a], bx[6 + a]);
-            }
-        }
-        const long long cnt = w.end - w.begin;
-        if (cnt <= kLeafSize) {
-            nd.first = static_cast<int>(w.begin);
-            nd.count = static_cast<int>(cnt);
-            b.nodes[w.node] = nd;
-            continue;
-        }
-        if (w.depth + 1 >= kMeshStack) {
-            b.err = "mesh BVH too deep";
-            return false;
-        }
-        int axis = 0;
-        for (int a = 1; a < 3; ++a)
-            if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
-        const long long mid = w.begin + cnt / 2;
-        std::nth_element(idx.begin() + w.begin, idx.begin() + mid, idx.begin() + w.end,
-                         [&](long long x, long long y) { return box[x][6 + axis] < box[y][6 + axis]; });
-        nd.first = static_cast<int>(b.nodes.size());
-        nd.count = 0;
-        b.nodes[w.node] = nd;
-        b.nodes.push_back(MeshNode{});
-        b.nodes.push_back(MeshNode{});
-        stack.push_back({nd.first + 1, mid, w.end, w.depth + 1});
-        stack.push_back({nd.first, w.begin, mid, w.depth + 1});
-    }
+    b.nodes.reserve(static_cast<size_t>(2 * (n / 2 + 1)));
+    B.nodes = &b.nodes;
+    B.build(0, n);
     std::vector<long long> ordered(n);
-    for (long long i = 0; i < n; ++i) ordered[i] = b.elems[idx[i]];
+    for (long long i = 0; i < n; ++i) ordered[i] = b.elems[B.idx[i]];
     b.elems.swap(ordered);
     return true;
 }
