@@ -17,10 +17,20 @@ namespace {
 
 using dev::find_brick;
 
+// 32 bytes at a 32-byte aligned address in one 256-bit load (sm_100 and later)
+__device__ __forceinline__ void ldg256(const float4 *p, float4 &a, float4 &b)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // Smallest barycentric coordinate of q in the element (record at rec).
 __device__ __forceinline__ float min_bary(const float4 *rec, float qx, float qy, float qz)
 {
-    const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2), r3 = __ldg(rec + 3);
+    float4 r0, r1, r2, r3;
+    ldg256(rec, r0, r1);
+    ldg256(rec + 2, r2, r3);
     const float dx = qx - r0.x, dy = qy - r0.y, dz = qz - r0.z;
     const float l1 = fmaf(r1.x, dx, fmaf(r1.y, dy, fmaf(r1.z, dz, 0.25f)));
     const float l2 = fmaf(r2.x, dx, fmaf(r2.y, dy, fmaf(r2.z, dz, 0.25f)));
@@ -66,8 +76,9 @@ __device__ int locate(const MeshParams &p, int brick, float qx, float qy, float 
     return best;
 }
 
+// 7 blocks of 128 threads per SM: at most 72 registers per thread
 template <bool COUNT, bool OPC>
-__global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__ MeshParams P)
+__global__ void __launch_bounds__(128, 7) march_mesh_kernel(const __grid_constant__ MeshParams P)
 {
     const MarchParams &p = P.m;
     const int item = blockIdx.x;
@@ -103,12 +114,15 @@ __global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__
         }
         bool forced = true;  // a located element takes its first sample unconditionally
         int stall = 0;
-        // One element per iteration: every lane loads its element (the same
-        // instruction stream for the warp), then takes the element's samples.
+        float4 r0, r1, r2, r3;
+        ldg256(rec + kMeshRec * e, r0, r1);
+        ldg256(rec + kMeshRec * e + 2, r2, r3);
+        int4 nb = __ldg(nbr + e);
+        // One element per iteration: every lane handles its current element
+        // (the same instruction stream for the warp), requests the next
+        // element's record, then takes the current element's samples while
+        // that request is in flight.
         while (true) {
-            const float4 *r = rec + kMeshRec * e;
-            const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
-            const int4 nb = __ldg(nbr + e);  // needed after the samples: issued early
             // exit parameter: smallest t at which a decreasing barycentric
             // coordinate reaches 0, measured from the current sample position
             const float dx = qx - r0.x, dy = qy - r0.y, dz = qz - r0.z;
@@ -132,6 +146,14 @@ __global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__
             const float gx = fmaf(r1.w, r1.x, fmaf(r2.w, r2.x, r3.w * r3.x));
             const float gy = fmaf(r1.w, r1.y, fmaf(r2.w, r2.y, r3.w * r3.y));
             const float gz = fmaf(r1.w, r1.z, fmaf(r2.w, r2.z, r3.w * r3.z));
+            // the element after this one, requested before this one's samples
+            int nx = face == 0 ? nb.x : face == 1 ? nb.y : face == 2 ? nb.z : face == 3 ? nb.w : -1;
+            const int pe = nx >= 0 ? nx : e;
+            const float4 *pr = rec + kMeshRec * pe;  // re-pointed after a locate
+            float4 p0, p1, p2, p3;
+            ldg256(pr, p0, p1);
+            ldg256(pr + 2, p2, p3);
+            int4 pn = __ldg(nbr + pe);
             bool done = false;
             while (forced || t <= t_exit) {
                 forced = false;
@@ -140,7 +162,8 @@ __global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__
                 const float x = fminf(fmaxf(fmaf(s, p.tf_scale, p.tf_bias), 0.0f), xmax);
                 const int ti = static_cast<int>(x);
                 const float w = x - static_cast<float>(ti);
-                const float4 e0 = __ldg(tf + 2 * ti), de = __ldg(tf + 2 * ti + 1);
+                float4 e0, de;
+                ldg256(tf + 2 * ti, e0, de);
                 float al = fmaf(w, de.w, e0.w);
                 if (OPC) al = -expm1f(p.opc_ratio * log1pf(-al));
                 const float ta = T * al;
@@ -163,7 +186,6 @@ __global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__
             // the next sample lies beyond this element: the neighbour across the
             // exit face, or a new point location after a boundary face or too
             // many steps without a sample (rounding near edges and vertices)
-            int nx = face == 0 ? nb.x : face == 1 ? nb.y : face == 2 ? nb.z : face == 3 ? nb.w : -1;
             if (nx < 0 || ++stall > kMeshStallSteps) {
                 nx = locate(P, bi, qx, qy, qz);
                 if (nx < 0) {
@@ -171,8 +193,14 @@ __global__ void __launch_bounds__(128) march_mesh_kernel(const __grid_constant__
                     nx = e;
                 }
                 forced = true;
+                pr = rec + kMeshRec * nx;
+                ldg256(pr, p0, p1);
+                ldg256(pr + 2, p2, p3);
+                pn = __ldg(nbr + nx);
             }
             e = nx;
+            r0 = p0; r1 = p1; r2 = p2; r3 = p3;
+            nb = pn;
         }
     }
     p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = make_float4(C0, C1, C2, 1.0f - T);
