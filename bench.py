@@ -429,8 +429,8 @@ def run_ours(a):
                       traffic=recorded_traffic() if a.workload == "paper" else None,
                       note="FP32 %d flops/sample x executed samples / mean march launch; peak = 152 SMs x "
                            "128 lanes x 2 x %.0f MHz (derived)" % (FLOPS_PER_SAMPLE, sm_max)),
-        roofline_l1=dict(note="ncu on the march: L1 data-pipe LSU wavefronts 70% of peak, SM issue "
-                              "67%, top stall long scoreboard (profiles/march_paper_workload.md)"),
+        roofline_l1=dict(note="ncu on the march: L1 data-pipe LSU wavefronts 74% of peak, issue slots "
+                              "61%, top stall long scoreboard (profiles/march_paper_workload.md)"),
         roofline_hbm=dict(march=dict(achieved=march_hbm_gbs, peak=hbm, unit="GB/s", frac=march_hbm_gbs / hbm,
                                      note="compulsory bytes (volume once + partial writes) / march time, %s"
                                           % hbm_src),

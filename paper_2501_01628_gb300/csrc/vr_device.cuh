@@ -196,11 +196,67 @@ __device__ __forceinline__ void owned_run(const P &p, const BrickLaunch &B, int 
     brick_run(p, B, ray, run);
 }
 
+// Packed FP32 pairs (sm_100 family): two lanes of one 64-bit register, each
+// rounded as the scalar instruction would be.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// a + b rounded towards -infinity in both lanes
+__device__ __forceinline__ unsigned long long f2_add_rm(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// floor by the 1.5 * 2^23 offset: for |v| < 2^22, y = v + 1.5 * 2^23 rounded
+// towards -infinity is exactly 1.5 * 2^23 + floor(v), whose bit pattern is
+// kFloorBits + floor(v) (the binade of y has unit spacing).
+constexpr float kFloorOffset = 12582912.0f;
+constexpr unsigned kFloorBits = 0x4B400000u;
+
+// 32 bytes at a 32-byte aligned address in one 256-bit load (sm_100 and later)
+__device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // Front-to-back emission-absorption over one owned run (see include/vr.h):
 // C += T alpha rgb, T *= (1 - alpha), continuing from the state (C, T) passed
-// in, and stopping once T <= ert_T. The two samples of an iteration request
-// their cells' quads before either is classified, and a sample in the previous
-// sample's cell reuses its quads.
+// in, and stopping once T <= ert_T.
+//
+// The samples go in pairs (k, k+1). The pair's positions, floors and weights
+// are computed in packed FP32 lanes; floors use the 1.5 * 2^23 offset, so the
+// floor's bit pattern gives the cell without a conversion. The quad index is
+// the blocked layout's (quad_index) written as a sum of per-axis terms,
+//   4i - 3(i&1) + 4 nbx j + (2 - 4 nbx)(j&1) + 4 nbx nby k + (4 - 4 nbx nby)(k&1),
+// evaluated on the floors' bit patterns, and plane k+1's quad lies
+// 4 + (k&1)(8 nbx nby - 8) further on; both are clamped to the brick's storage
+// (owned samples always lie inside the brick, so the clamp only guards memory).
+// Both cells' quads are requested before either sample is classified, a sample
+// in the previous sample's cell reuses its quads, and both samples'
+// transfer-function pairs are requested before the first is accumulated.
 // OPC: opacity correction for a step other than the reference step,
 // alpha' = 1 - (1 - alpha)^ratio, evaluated as -expm1(ratio * log1p(-alpha)).
 template <typename S, bool COUNT, bool OPC = false>
@@ -209,82 +265,107 @@ __device__ __forceinline__ void march_accumulate(const void *data, const BrickLa
                                                  float ert_T, float &C0, float &C1, float &C2, float &T,
                                                  unsigned long long &executed, float opc_ratio = 1.0f)
 {
-    {
-        const int ka = run.ka, kb = run.kb;
-        // owned samples are contiguous along the ray: [ka, kb] are all owned
-        if (ka <= kb) {
-            using Q = typename Quad<S>::type;
-            const Q *vox = static_cast<const Q *>(data) + B.base;
-            const int nbx = B.sx / 2, nby = B.sy / 2;
-            const int imax = B.hi[0] - B.lo[0], jmax = B.hi[1] - B.lo[1], kmax = B.hi[2] - B.lo[2];
-            const float xmax = static_cast<float>(ntf - 1);
-            const float *base = run.base, *step = run.step;
-            // two samples per iteration: both cells' loads are issued before either
-            // sample is classified (independent memory requests in flight)
-            int prev = -1;
-            float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
-            float kh = static_cast<float>(ka) + 0.5f;
-            // quad indices of planes k and k+1 of the sample's cell; the clamps
-            // only guard memory (owned samples always lie inside the brick)
-            auto locate = [&](float h, int &cell, int &cell1, float &wx, float &wy, float &wz) {
-                const float vx = fmaf(h, step[0], base[0]);
-                const float vy = fmaf(h, step[1], base[1]);
-                const float vz = fmaf(h, step[2], base[2]);
-                const float flx = floorf(vx), fly = floorf(vy), flz = floorf(vz);
-                wx = vx - flx;
-                wy = vy - fly;
-                wz = vz - flz;
-                const int i = min(max(static_cast<int>(flx), 0), imax);
-                const int j = min(max(static_cast<int>(fly), 0), jmax);
-                const int k = min(max(static_cast<int>(flz), 0), kmax);
-                cell = quad_index(i, j, k, nbx, nby);
-                cell1 = quad_index(i, j, k + 1, nbx, nby);
-            };
-            auto shade = [&](const float4 &a0, const float4 &a1, float wx, float wy, float wz) {
-                const float c00 = fmaf(wx, a0.y - a0.x, a0.x), c10 = fmaf(wx, a0.w - a0.z, a0.z);
-                const float c01 = fmaf(wx, a1.y - a1.x, a1.x), c11 = fmaf(wx, a1.w - a1.z, a1.z);
-                const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
-                const float s = fmaf(wz, c1 - c0, c0);
-                const float x = fminf(fmaxf(fmaf(s, tf_scale, tf_bias), 0.0f), xmax);
-                const int ti = static_cast<int>(x);
-                const float w = x - static_cast<float>(ti);
-                const float4 e0 = __ldg(tf + 2 * ti), de = __ldg(tf + 2 * ti + 1);
-                const float r = fmaf(w, de.x, e0.x), g = fmaf(w, de.y, e0.y);
-                const float bb = fmaf(w, de.z, e0.z);
-                float al = fmaf(w, de.w, e0.w);
-                if (OPC) al = -expm1f(opc_ratio * log1pf(-al));
-                const float ta = T * al;
-                C0 = fmaf(ta, r, C0);
-                C1 = fmaf(ta, g, C1);
-                C2 = fmaf(ta, bb, C2);
-                T = T - ta;
-            };
-            for (int k = ka; k <= kb; k += 2, kh += 2.0f) {
-                int ca, ca1, cb, cb1;
-                float ax, ay, az, bx, by, bz;
-                locate(kh, ca, ca1, ax, ay, az);
-                const bool two = k < kb;
-                locate(kh + 1.0f, cb, cb1, bx, by, bz);
-                if (ca != prev) {
-                    q0 = Quad<S>::load(vox + ca);
-                    q1 = Quad<S>::load(vox + ca1);
-                }
-                float4 r0 = q0, r1 = q1;
-                if (two && cb != ca) {
-                    r0 = Quad<S>::load(vox + cb);
-                    r1 = Quad<S>::load(vox + cb1);
-                }
-                shade(q0, q1, ax, ay, az);
-                if (COUNT) ++executed;
-                if (T <= ert_T || !two) break;
-                shade(r0, r1, bx, by, bz);
-                if (COUNT) ++executed;
-                if (T <= ert_T) break;
-                q0 = r0;
-                q1 = r1;
-                prev = cb;
-            }
+    const int ka = run.ka, kb = run.kb;
+    if (ka > kb) return;
+    using Q = typename Quad<S>::type;
+    const Q *vox = static_cast<const Q *>(data) + B.base;
+    const unsigned nbx = static_cast<unsigned>(B.sx / 2), nby = static_cast<unsigned>(B.sy / 2);
+    const unsigned nbz = static_cast<unsigned>(B.hi[2] - B.lo[2] + 3) / 2;
+    const unsigned last = nbx * nby * nbz * 8u - 1u;  // last quad of the brick's storage
+    const unsigned ay = 4u * nbx, az = 4u * nbx * nby;
+    const unsigned c0 = 0u - (4u + ay + az) * kFloorBits;  // removes the offsets' bits
+    const unsigned py = 2u - ay, pz = 4u - az, dz = 2u * az - 8u;
+    const float xmax = static_cast<float>(ntf - 1);
+    // transfer-function pair i at tf + 2 i, addressed from the floor's bits
+    const uintptr_t tf_base = reinterpret_cast<uintptr_t>(tf) - static_cast<uintptr_t>(kFloorBits) * 32u;
+    const unsigned long long off2 = f2_pack(kFloorOffset, kFloorOffset);
+    const unsigned long long st_x = f2_pack(run.step[0], run.step[0]), bs_x = f2_pack(run.base[0], run.base[0]);
+    const unsigned long long st_y = f2_pack(run.step[1], run.step[1]), bs_y = f2_pack(run.base[1], run.base[1]);
+    const unsigned long long st_z = f2_pack(run.step[2], run.step[2]), bs_z = f2_pack(run.base[2], run.base[2]);
+    const unsigned long long tfs2 = f2_pack(tf_scale, tf_scale), tfb2 = f2_pack(tf_bias, tf_bias);
+    // quad indices of the cell (plane k) and of plane k+1 from the floors' bits
+    auto cells = [&](unsigned bx, unsigned by, unsigned bz, unsigned &cell, unsigned &cell1) {
+        unsigned c = bz * az + c0;
+        c = by * ay + c;
+        c = bx * 4u + c;
+        c = (bx & 1u) * (0u - 3u) + c;
+        c = (by & 1u) * py + c;
+        c = (bz & 1u) * pz + c;
+        cell1 = min(c + 4u + (bz & 1u) * dz, last);
+        cell = min(c, last);
+    };
+    auto trilinear = [&](const float4 &a0, const float4 &a1, float wx, float wy, float wz) {
+        const float c00 = fmaf(wx, a0.y - a0.x, a0.x), c10 = fmaf(wx, a0.w - a0.z, a0.z);
+        const float c01 = fmaf(wx, a1.y - a1.x, a1.x), c11 = fmaf(wx, a1.w - a1.z, a1.z);
+        const float c0_ = fmaf(wy, c10 - c00, c00), c1_ = fmaf(wy, c11 - c01, c01);
+        return fmaf(wz, c1_ - c0_, c0_);
+    };
+    auto accumulate = [&](const float4 &e0, const float4 &de, float w) {
+        const float r = fmaf(w, de.x, e0.x), g = fmaf(w, de.y, e0.y);
+        const float bb = fmaf(w, de.z, e0.z);
+        float al = fmaf(w, de.w, e0.w);
+        if (OPC) al = -expm1f(opc_ratio * log1pf(-al));
+        const float ta = T * al;
+        C0 = fmaf(ta, r, C0);
+        C1 = fmaf(ta, g, C1);
+        C2 = fmaf(ta, bb, C2);
+        T = T - ta;
+    };
+    unsigned prev = 0xffffffffu;
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+    float kh = static_cast<float>(ka) + 0.5f;
+    for (int k = ka; k <= kb; k += 2, kh += 2.0f) {
+        const bool two = k < kb;
+        // positions (voxel-centre coordinates) of samples k and k+1, their
+        // floors (offset form) and weights
+        const unsigned long long h2 = f2_pack(kh, kh + 1.0f);
+        const unsigned long long vx = f2_fma(h2, st_x, bs_x), vy = f2_fma(h2, st_y, bs_y),
+                                 vz = f2_fma(h2, st_z, bs_z);
+        const unsigned long long yx = f2_add_rm(vx, off2), yy = f2_add_rm(vy, off2), yz = f2_add_rm(vz, off2);
+        float ax, bx_, ay_, by_, az_, bz_;
+        f2_unpack(f2_sub(vx, f2_sub(yx, off2)), ax, bx_);
+        f2_unpack(f2_sub(vy, f2_sub(yy, off2)), ay_, by_);
+        f2_unpack(f2_sub(vz, f2_sub(yz, off2)), az_, bz_);
+        float fxa, fxb, fya, fyb, fza, fzb;
+        f2_unpack(yx, fxa, fxb);
+        f2_unpack(yy, fya, fyb);
+        f2_unpack(yz, fza, fzb);
+        unsigned ca, ca1, cb, cb1;
+        cells(__float_as_uint(fxa), __float_as_uint(fya), __float_as_uint(fza), ca, ca1);
+        cells(__float_as_uint(fxb), __float_as_uint(fyb), __float_as_uint(fzb), cb, cb1);
+        if (ca != prev) {
+            q0 = Quad<S>::load(vox + ca);
+            q1 = Quad<S>::load(vox + ca1);
         }
+        float4 r0 = q0, r1 = q1;
+        if (two && cb != ca) {
+            r0 = Quad<S>::load(vox + cb);
+            r1 = Quad<S>::load(vox + cb1);
+        }
+        // both samples' table coordinates x = clamp((s - vmin)/(vmax - vmin), 0, 1)(n - 1)
+        const float sa = trilinear(q0, q1, ax, ay_, az_);
+        const float sb = trilinear(r0, r1, bx_, by_, bz_);
+        float xa, xb;
+        f2_unpack(f2_fma(f2_pack(sa, sb), tfs2, tfb2), xa, xb);
+        xa = fminf(fmaxf(xa, 0.0f), xmax);
+        xb = fminf(fmaxf(xb, 0.0f), xmax);
+        const unsigned long long x2 = f2_pack(xa, xb);
+        const unsigned long long y2 = f2_add_rm(x2, off2);
+        float wa, wb, ya, yb;
+        f2_unpack(f2_sub(x2, f2_sub(y2, off2)), wa, wb);
+        f2_unpack(y2, ya, yb);
+        float4 ea, da, eb, db;
+        ldg_v8(reinterpret_cast<const float4 *>(tf_base + static_cast<uintptr_t>(__float_as_uint(ya)) * 32u), ea, da);
+        ldg_v8(reinterpret_cast<const float4 *>(tf_base + static_cast<uintptr_t>(__float_as_uint(yb)) * 32u), eb, db);
+        accumulate(ea, da, wa);
+        if (COUNT) ++executed;
+        if (T <= ert_T || !two) break;
+        accumulate(eb, db, wb);
+        if (COUNT) ++executed;
+        if (T <= ert_T) break;
+        q0 = r0;
+        q1 = r1;
+        prev = cb;
     }
 }
 

@@ -16,21 +16,14 @@ namespace vr {
 namespace {
 
 using dev::find_brick;
-
-// 32 bytes at a 32-byte aligned address in one 256-bit load (sm_100 and later)
-__device__ __forceinline__ void ldg256(const float4 *p, float4 &a, float4 &b)
-{
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-        : "l"(p));
-}
+using dev::ldg_v8;
 
 // Smallest barycentric coordinate of q in the element (record at rec).
 __device__ __forceinline__ float min_bary(const float4 *rec, float qx, float qy, float qz)
 {
     float4 r0, r1, r2, r3;
-    ldg256(rec, r0, r1);
-    ldg256(rec + 2, r2, r3);
+    ldg_v8(rec, r0, r1);
+    ldg_v8(rec + 2, r2, r3);
     const float dx = qx - r0.x, dy = qy - r0.y, dz = qz - r0.z;
     const float l1 = fmaf(r1.x, dx, fmaf(r1.y, dy, fmaf(r1.z, dz, 0.25f)));
     const float l2 = fmaf(r2.x, dx, fmaf(r2.y, dy, fmaf(r2.z, dz, 0.25f)));
@@ -115,8 +108,8 @@ __global__ void __launch_bounds__(128, 7) march_mesh_kernel(const __grid_constan
         bool forced = true;  // a located element takes its first sample unconditionally
         int stall = 0;
         float4 r0, r1, r2, r3;
-        ldg256(rec + kMeshRec * e, r0, r1);
-        ldg256(rec + kMeshRec * e + 2, r2, r3);
+        ldg_v8(rec + kMeshRec * e, r0, r1);
+        ldg_v8(rec + kMeshRec * e + 2, r2, r3);
         int4 nb = __ldg(nbr + e);
         // One element per iteration: every lane handles its current element
         // (the same instruction stream for the warp), requests the next
@@ -151,8 +144,8 @@ __global__ void __launch_bounds__(128, 7) march_mesh_kernel(const __grid_constan
             const int pe = nx >= 0 ? nx : e;
             const float4 *pr = rec + kMeshRec * pe;  // re-pointed after a locate
             float4 p0, p1, p2, p3;
-            ldg256(pr, p0, p1);
-            ldg256(pr + 2, p2, p3);
+            ldg_v8(pr, p0, p1);
+            ldg_v8(pr + 2, p2, p3);
             int4 pn = __ldg(nbr + pe);
             bool done = false;
             while (forced || t <= t_exit) {
@@ -163,7 +156,7 @@ __global__ void __launch_bounds__(128, 7) march_mesh_kernel(const __grid_constan
                 const int ti = static_cast<int>(x);
                 const float w = x - static_cast<float>(ti);
                 float4 e0, de;
-                ldg256(tf + 2 * ti, e0, de);
+                ldg_v8(tf + 2 * ti, e0, de);
                 float al = fmaf(w, de.w, e0.w);
                 if (OPC) al = -expm1f(p.opc_ratio * log1pf(-al));
                 const float ta = T * al;
@@ -194,8 +187,8 @@ __global__ void __launch_bounds__(128, 7) march_mesh_kernel(const __grid_constan
                 }
                 forced = true;
                 pr = rec + kMeshRec * nx;
-                ldg256(pr, p0, p1);
-                ldg256(pr + 2, p2, p3);
+                ldg_v8(pr, p0, p1);
+                ldg_v8(pr + 2, p2, p3);
                 pn = __ldg(nbr + nx);
             }
             e = nx;
