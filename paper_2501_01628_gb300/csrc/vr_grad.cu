@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(256) composite_grad_kernel(const __grid_consta
 // S-th sample, then segments back to front (forward recompute storing T_k,
 // then the per-sample adjoint). Table gradients gather in shared memory per
 // block; voxel gradients go to global memory with atomics on the global voxel
-// index (halo copies alias their neighbours' voxels).
+// index (halo copies alias their neighbours' voxels), once per run of samples
+// in one cell.
 template <typename S>
 __global__ void __launch_bounds__(128) march_grad_kernel(const __grid_constant__ MarchParams p, GradArgs ga)
 {
@@ -166,6 +167,42 @@ __global__ void __launch_bounds__(128) march_grad_kernel(const __grid_constant__
         const int nseg = (n + seg - 1) / seg;
         float lamT = -gp.w;
         float Ts[kMaxSeg];
+        // voxel gradients of consecutive samples in one cell are summed in
+        // registers and added to global memory once per cell (8 atomics)
+        int cur_i = -1, cur_j = 0, cur_k = 0;
+        float acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+        // likewise table gradients of consecutive samples in one table interval
+        // (entries ti and ti + 1) are summed before the shared-memory atomics
+        int cur_ti = -1;
+        float at0[4], at1[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) at0[c] = at1[c] = 0.0f;
+        auto flush_tf = [&]() {
+            if (cur_ti < 0) return;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                atomicAdd(&s_gtf[4 * cur_ti + c], at0[c]);
+                if (cur_ti + 1 < p.ntf && at1[c] != 0.0f) atomicAdd(&s_gtf[4 * (cur_ti + 1) + c], at1[c]);
+            }
+        };
+        auto flush = [&]() {
+            if (cur_i < 0) return;
+            const int gx0 = min(max(B.lo[0] - 1 + cur_i, 0), ga.N[0] - 1), gx1 = min(max(B.lo[0] + cur_i, 0), ga.N[0] - 1);
+            const int gy0 = min(max(B.lo[1] - 1 + cur_j, 0), ga.N[1] - 1), gy1 = min(max(B.lo[1] + cur_j, 0), ga.N[1] - 1);
+            const int gz0 = min(max(B.lo[2] - 1 + cur_k, 0), ga.N[2] - 1), gz1 = min(max(B.lo[2] + cur_k, 0), ga.N[2] - 1);
+            const long long nx = ga.N[0], nxy = static_cast<long long>(ga.N[0]) * ga.N[1];
+            float *gv = ga.grad_vol;
+            atomicAdd(gv + gz0 * nxy + gy0 * nx + gx0, acc[0]);
+            atomicAdd(gv + gz0 * nxy + gy0 * nx + gx1, acc[1]);
+            atomicAdd(gv + gz0 * nxy + gy1 * nx + gx0, acc[2]);
+            atomicAdd(gv + gz0 * nxy + gy1 * nx + gx1, acc[3]);
+            atomicAdd(gv + gz1 * nxy + gy0 * nx + gx0, acc[4]);
+            atomicAdd(gv + gz1 * nxy + gy0 * nx + gx1, acc[5]);
+            atomicAdd(gv + gz1 * nxy + gy1 * nx + gx0, acc[6]);
+            atomicAdd(gv + gz1 * nxy + gy1 * nx + gx1, acc[7]);
+        };
         for (int sg = nseg - 1; sg >= 0; --sg) {
             const int k0 = run.ka + sg * seg, k1 = min(run.kb, k0 + seg - 1);
             float t = ck[sg];
@@ -187,31 +224,43 @@ __global__ void __launch_bounds__(128) march_grad_kernel(const __grid_constant__
                 lamT = lamT * (1.0f - a) + a * gdotc;
                 // table: rgba = (1-w) T[i] + w T[i+1]
                 const float w0 = 1.0f - q.w;
+                if (q.ti != cur_ti) {
+                    flush_tf();
+                    cur_ti = q.ti;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) at0[c] = at1[c] = 0.0f;
+                }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    atomicAdd(&s_gtf[4 * q.ti + c], w0 * g4[c]);
-                    if (q.ti + 1 < p.ntf && q.w != 0.0f) atomicAdd(&s_gtf[4 * (q.ti + 1) + c], q.w * g4[c]);
+                    at0[c] = fmaf(w0, g4[c], at0[c]);
+                    at1[c] = fmaf(q.w, g4[c], at1[c]);
                 }
                 // scalar: ds = (g . (T[i+1] - T[i])) dx/ds where the table coordinate is not clamped
                 if (ga.grad_vol && q.x > 0.0f && q.x < xmax) {
                     const float ds = (g4[0] * q.de.x + g4[1] * q.de.y + g4[2] * q.de.z + g4[3] * q.de.w) * p.tf_scale;
-                    const int gx0 = min(max(B.lo[0] - 1 + q.i, 0), ga.N[0] - 1), gx1 = min(max(B.lo[0] + q.i, 0), ga.N[0] - 1);
-                    const int gy0 = min(max(B.lo[1] - 1 + q.j, 0), ga.N[1] - 1), gy1 = min(max(B.lo[1] + q.j, 0), ga.N[1] - 1);
-                    const int gz0 = min(max(B.lo[2] - 1 + q.k, 0), ga.N[2] - 1), gz1 = min(max(B.lo[2] + q.k, 0), ga.N[2] - 1);
-                    const long long nx = ga.N[0], nxy = static_cast<long long>(ga.N[0]) * ga.N[1];
+                    if (q.i != cur_i || q.j != cur_j || q.k != cur_k) {
+                        flush();
+                        cur_i = q.i;
+                        cur_j = q.j;
+                        cur_k = q.k;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+                    }
                     const float ux = 1.0f - q.wx, uy = 1.0f - q.wy, uz = 1.0f - q.wz;
-                    float *gv = ga.grad_vol;
-                    atomicAdd(gv + gz0 * nxy + gy0 * nx + gx0, ds * ux * uy * uz);
-                    atomicAdd(gv + gz0 * nxy + gy0 * nx + gx1, ds * q.wx * uy * uz);
-                    atomicAdd(gv + gz0 * nxy + gy1 * nx + gx0, ds * ux * q.wy * uz);
-                    atomicAdd(gv + gz0 * nxy + gy1 * nx + gx1, ds * q.wx * q.wy * uz);
-                    atomicAdd(gv + gz1 * nxy + gy0 * nx + gx0, ds * ux * uy * q.wz);
-                    atomicAdd(gv + gz1 * nxy + gy0 * nx + gx1, ds * q.wx * uy * q.wz);
-                    atomicAdd(gv + gz1 * nxy + gy1 * nx + gx0, ds * ux * q.wy * q.wz);
-                    atomicAdd(gv + gz1 * nxy + gy1 * nx + gx1, ds * q.wx * q.wy * q.wz);
+                    const float dz0 = ds * uz, dz1 = ds * q.wz;
+                    acc[0] = fmaf(dz0, ux * uy, acc[0]);
+                    acc[1] = fmaf(dz0, q.wx * uy, acc[1]);
+                    acc[2] = fmaf(dz0, ux * q.wy, acc[2]);
+                    acc[3] = fmaf(dz0, q.wx * q.wy, acc[3]);
+                    acc[4] = fmaf(dz1, ux * uy, acc[4]);
+                    acc[5] = fmaf(dz1, q.wx * uy, acc[5]);
+                    acc[6] = fmaf(dz1, ux * q.wy, acc[6]);
+                    acc[7] = fmaf(dz1, q.wx * q.wy, acc[7]);
                 }
             }
         }
+        if (ga.grad_vol) flush();
+        flush_tf();
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * p.ntf; i += blockDim.x)
