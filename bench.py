@@ -73,17 +73,18 @@ def reduce_job(ms: float, e2e_s: float, samples: float, world: int, device: str 
     return float(mx[0]), float(mx[1]), float(sm[0])
 
 
-def recorded_traffic():
-    """DRAM bytes per march launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def recorded_traffic(summary: str = "march_paper_workload.md",
+                     sources=("vr_kernels.cu", "vr_device.cuh", "vr_internal.h")):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, if the
+    summary was taken on the current kernel source (else None)."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "march_paper_workload.md")
+    path = os.path.join(ROOT, "profiles", summary)
     csrc = os.path.join(ROOT, "paper_2501_01628_gb300", "csrc")
     try:
         text = open(path).read()
         h = hashlib.sha256()
-        for f in ("vr_kernels.cu", "vr_device.cuh", "vr_internal.h"):
+        for f in sources:
             h.update(open(os.path.join(csrc, f), "rb").read())
     except OSError:
         return None
@@ -92,6 +93,9 @@ def recorded_traffic():
     if not m or not k or k.group(1) != h.hexdigest()[:16]:
         return None
     return float(m.group(1))
+
+
+MESH_SOURCES = ("vr_mesh.cu", "vr_mesh.h", "vr_device.cuh", "vr_internal.h")
 
 
 def workload(name: str):
@@ -892,7 +896,7 @@ def run_mesh(a):
                     % (mesh_bytes / 1e9), parallelism="1 GPU"),
         frames_per_s=K / (ms / 1e3), samples_per_frame=samples / K, gpu_launches=2 * K, clocks=clk,
         roofline=dict(bound="hbm", kernel="march_mesh", achieved=march_gbs, peak=hbm, unit="GB/s",
-                      frac=march_gbs / hbm, traffic=None,
+                      frac=march_gbs / hbm, traffic=recorded_traffic("mesh_workload.md", MESH_SOURCES),
                       note="upper-bound compulsory bytes (whole mesh once + partial writes) / mean march "
                            "launch, %s; the walk is latency-bound (dependent element loads)" % hbm_src),
         kernel_ms=dict(march=march_ms, composite=comp_ms), mesh_create_s=create_s, mesh_device_bytes=mesh_bytes,
