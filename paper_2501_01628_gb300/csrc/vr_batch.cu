@@ -44,7 +44,7 @@ __device__ __forceinline__ bool wait_at_least(const int *addr, int target, int l
 }
 
 template <typename S, bool OPC>
-__global__ void __launch_bounds__(128, 10) batch_kernel(const __grid_constant__ BatchParams p)
+__global__ void __launch_bounds__(128, 9) batch_kernel(const __grid_constant__ BatchParams p)
 {
     __shared__ long long s_item;
     __shared__ int s_brick[kMaxBricks];
