@@ -69,9 +69,9 @@ __device__ int locate(const MeshParams &p, int brick, float qx, float qy, float 
     return best;
 }
 
-// 7 blocks of 128 threads per SM: at most 72 registers per thread
+// 8 blocks of 128 threads per SM: at most 64 registers per thread
 template <bool COUNT, bool OPC>
-__global__ void __launch_bounds__(128, 7) march_mesh_kernel(const __grid_constant__ MeshParams P)
+__global__ void __launch_bounds__(128, 8) march_mesh_kernel(const __grid_constant__ MeshParams P)
 {
     const MarchParams &p = P.m;
     const int item = blockIdx.x;
