@@ -17,9 +17,12 @@ constexpr int kMaxFactors = 8;
 // parameter, MarchParams::pw).
 constexpr int kTileW = 16;
 constexpr int kTileH = 8;
-// Composite tile: 32 x 8 pixels per 256-thread block.
+// Composite: 256-thread blocks of 32 x 8 threads. The forward composite gives a
+// block a tile of kCompRows such 32 x 8 halves, stacked (one brick list per
+// 32 x 16 tile); the composite adjoint takes 32 x 8 tiles.
 constexpr int kCompW = 32;
 constexpr int kCompH = 8;
+constexpr int kCompRows = 2;
 
 // Brick storage index of quad (i, j, k): quads are grouped in 2x2x2 blocks of
 // 128 bytes (one L1 line for float32), blocks x-fastest; nbx, nby = blocks per

@@ -106,8 +106,9 @@ __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Composite: one block per 32x8 image tile, one thread per pixel; partials are
-// combined front to back with "over" along the configured association tree.
+// Composite: one 32x8-thread block per 32x16 image tile, one thread per pixel
+// of each of the tile's two 32x8 halves; partials are combined front to back
+// with "over" along the configured association tree.
 // ---------------------------------------------------------------------------
 // Per tile, warp 0 first compacts the bricks whose rectangles overlap the tile,
 // in visibility order. Absent partials are the identity of "over", so only the
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
     __shared__ int s_pos[kMaxBricks + 1];
     __shared__ unsigned char s_carry[kMaxBricks];
     __shared__ int s_m;
-    const int tx0 = blockIdx.x * kCompW, ty0 = blockIdx.y * kCompH;
+    const int tx0 = blockIdx.x * kCompW, ty0 = blockIdx.y * (kCompH * kCompRows);
     const int tid = threadIdx.y * kCompW + threadIdx.x;
     if (tid < 32) {
         int m = 0;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
             if (j < p.nb) {
                 b = p.order[j];
                 const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
-                ov = x0 < tx0 + kCompW && tx0 < x0 + w && y0 < ty0 + kCompH && ty0 < y0 + h;
+                ov = x0 < tx0 + kCompW && tx0 < x0 + w && y0 < ty0 + kCompH * kCompRows && ty0 < y0 + h;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, ov);
             if (ov) {
@@ -157,47 +158,50 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
     }
     __syncthreads();
     const int m = s_m;
-    const int px = tx0 + threadIdx.x, py = ty0 + threadIdx.y;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 acc[LEVELS];
+    const int px = tx0 + threadIdx.x;
+    for (int half = 0; half < kCompRows; ++half) {
+        const int py = ty0 + threadIdx.y + kCompH * half;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 acc[LEVELS];
 #pragma unroll
-    for (int l = 0; l < LEVELS; ++l) acc[l] = zero;
-    constexpr int kBatch = 4;  // partial loads in flight before they are combined
-    for (int i0 = 0; i0 < m; i0 += kBatch) {
-        float4 v[kBatch];
+        for (int l = 0; l < LEVELS; ++l) acc[l] = zero;
+        constexpr int kBatch = 4;  // partial loads in flight before they are combined
+        for (int i0 = 0; i0 < m; i0 += kBatch) {
+            float4 v[kBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            v[u] = zero;
-            if (i0 + u < m) {
-                const int b = s_brick[i0 + u];
-                const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
-                if (px >= x0 && px < x0 + w && py >= y0 && py < y0 + h)
-                    v[u] = __ldcs(p.partials + p.poff[b] + static_cast<long long>(py - y0) * w + (px - x0));
+            for (int u = 0; u < kBatch; ++u) {
+                v[u] = zero;
+                if (i0 + u < m) {
+                    const int b = s_brick[i0 + u];
+                    const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
+                    if (px >= x0 && px < x0 + w && py >= y0 && py < y0 + h)
+                        v[u] = __ldcs(p.partials + p.poff[b] + static_cast<long long>(py - y0) * w + (px - x0));
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            if (i0 + u < m) {
-                acc[0] = over(acc[0], v[u]);
-                if (LEVELS > 1) {
-                    const int c = s_carry[i0 + u];
+            for (int u = 0; u < kBatch; ++u) {
+                if (i0 + u < m) {
+                    acc[0] = over(acc[0], v[u]);
+                    if (LEVELS > 1) {
+                        const int c = s_carry[i0 + u];
 #pragma unroll
-                    for (int l = 0; l + 1 < LEVELS; ++l) {
-                        if (l < c) {
-                            acc[l + 1] = over(acc[l + 1], acc[l]);
-                            acc[l] = zero;
+                        for (int l = 0; l + 1 < LEVELS; ++l) {
+                            if (l < c) {
+                                acc[l + 1] = over(acc[l + 1], acc[l]);
+                                acc[l] = zero;
+                            }
                         }
                     }
                 }
             }
         }
-    }
-    if (px < p.W && py < p.H) {
-        float4 r = acc[0];
+        if (px < p.W && py < p.H) {
+            float4 r = acc[0];
 #pragma unroll
-        for (int l = 1; l < LEVELS; ++l)
-            if (l == p.n_levels - 1) r = acc[l];
-        __stcs(p.out + static_cast<long long>(py) * p.W + px, r);
+            for (int l = 1; l < LEVELS; ++l)
+                if (l == p.n_levels - 1) r = acc[l];
+            __stcs(p.out + static_cast<long long>(py) * p.W + px, r);
+        }
     }
 }
 
@@ -266,7 +270,7 @@ cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s)
 {
     dim3 block(kCompW, kCompH);
-    dim3 grid((p.W + kCompW - 1) / kCompW, (p.H + kCompH - 1) / kCompH);
+    dim3 grid((p.W + kCompW - 1) / kCompW, (p.H + kCompH * kCompRows - 1) / (kCompH * kCompRows));
     if (p.W <= 0 || p.H <= 0) return cudaSuccess;
     if (p.n_levels <= 1) composite_kernel<1><<<grid, block, 0, s>>>(p);
     else if (p.n_levels <= 4) composite_kernel<4><<<grid, block, 0, s>>>(p);

@@ -151,6 +151,26 @@ def test_radix_k_schedules_agree(vr):
 # --------------------------------------------------------------------------
 
 
+
+def test_paper_workload_sampled(vr):
+    """The benchmark's configuration at full size: 512^3 value noise + blobs
+    (seed 1), 36 grid bricks, 1920x1080 perspective orbit views, step 0.5 voxel,
+    per-brick early termination at alpha 0.99, radix-k composite 4x3x3, 4x8-pixel
+    ray packets. 2048 random pixels of two views against the FP64 oracle."""
+    import torch
+    vol, tf = synth.noise_blob_scene()
+    lo, hi = synth.volume_range(vol)
+    part = dict(kind="grid", grid=(4, 3, 3))
+    boxes = oracle.grid_partition((512,) * 3, (4, 3, 3))
+    vol_dev = torch.from_numpy(vol).cuda()
+    for k, az in enumerate((synth.ORBIT_AZIMUTHS[0], synth.ORBIT_AZIMUTHS[3])):
+        cam = synth.orbit_camera(1920, 1080, az)
+        got = gpu_render(vr, vol_dev, part, tf, lo, hi, cam, 0.5, 0.99, schedule=(4, 3, 3))["img"]
+        prng = np.random.default_rng(30 + k)
+        pix = np.stack([prng.integers(0, 1920, 2048), prng.integers(0, 1080, 2048)], axis=1)
+        env = oracle_env(vol, boxes, tf, lo, hi, cam, 0.5, 0.99, pixels=pix)
+        compare_envelope(got[pix[:, 1], pix[:, 0]], env)
+
 @pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
 def test_pack_halo_exact(vr, storage):
     import torch
