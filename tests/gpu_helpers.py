@@ -9,7 +9,7 @@ TOL = 1e-4
 
 
 def gpu_render(vr, vol, part, tf, lo, hi, cam, step=0.5, ert=1.0, storage="f32", schedule=(),
-               count=False, partials=False, host_out=False):
+               count=False, partials=False, host_out=False, packet_width=None, mode=None):
     import torch
     ctx = vr.vr_create(0)
     v = None
@@ -20,6 +20,10 @@ def gpu_render(vr, vol, part, tf, lo, hi, cam, step=0.5, ert=1.0, storage="f32",
         vr.vr_set_render_params(ctx, step, ert)
         vr.vr_set_composite_schedule(ctx, schedule)
         vr.vr_set_count_samples(ctx, count)
+        if packet_width is not None:
+            vr.vr_set_packet_width(ctx, packet_width)
+        if mode is not None:
+            vr.vr_set_render_mode(ctx, mode)
         H, W = cam["height"], cam["width"]
         res = {}
         if partials:
