@@ -35,7 +35,7 @@ METRIC = "ray samples/s and composited frames/s at 1 GB300; % HBM roofline; vs F
 UNIT = "samples/s"
 # FP32 operations the method performs per executed sample (position 8,
 # trilinear reconstruction 30, classification 19, accumulation 8, termination
-# test 1); the derivation is in the design doc.
+# test 1).
 FLOPS_PER_SAMPLE = 66
 SMS, FP32_LANES = 152, 128
 
@@ -434,7 +434,7 @@ def run_ours(a):
                       note="FP32 %d flops/sample x executed samples / mean march launch; peak = 152 SMs x "
                            "128 lanes x 2 x %.0f MHz (derived)" % (FLOPS_PER_SAMPLE, sm_max)),
         roofline_l1=dict(note="ncu on the march: L1 data-pipe LSU wavefronts 74% of peak, issue slots "
-                              "61%, top stall long scoreboard (profiles/march_paper_workload.md)"),
+                              "61%, top stall long scoreboard"),
         roofline_hbm=dict(march=dict(achieved=march_hbm_gbs, peak=hbm, unit="GB/s", frac=march_hbm_gbs / hbm,
                                      note="compulsory bytes (volume once + partial writes) / march time, %s"
                                           % hbm_src),
