@@ -146,6 +146,33 @@ def test_radix_k_schedules_agree(vr):
         gpu_render(vr, vol, part, tf, lo, hi, cam, schedule=[5, 7])
 
 
+def test_maximum_bricks_and_deepest_radix_tree(vr):
+    """VR_MAX_BRICKS = 128 bricks (8x4x4 grid of a 64^3 volume): four 32-brick
+    chunks in the composite's tile compaction, a radix-k tree of seven factors
+    (the deepest association the composite supports), and the ray-state cycling
+    form over all 128 bricks; one brick more is refused."""
+    n = 64
+    rng = np.random.default_rng(23)
+    vol = synth.blob_volume(n, synth.draw_blobs(rng, 10))
+    tf = synth.random_tf(rng, alpha_max=0.1)
+    lo, hi = synth.volume_range(vol)
+    cam = synth.orbit_camera(96, 80, 33.0, elevation_deg=25.0)
+    part = dict(kind="grid", grid=(8, 4, 4))
+    boxes = oracle.grid_partition((n,) * 3, (8, 4, 4))
+    env = oracle_env(vol, boxes, tf, lo, hi, cam)
+    direct = gpu_render(vr, vol, part, tf, lo, hi, cam)["img"]
+    compare_envelope(direct, env)
+    for sched in ([2] * 7, [8, 16], [4, 4, 8]):
+        got = gpu_render(vr, vol, part, tf, lo, hi, cam, schedule=sched)["img"]
+        np.testing.assert_allclose(got, direct, atol=1e-6, rtol=0, err_msg=str(sched))
+    cyc = gpu_render(vr, vol, part, tf, lo, hi, cam, mode=1)["img"]
+    compare_envelope(cyc, env)
+    with pytest.raises(vr.VrError) as e:
+        gpu_render(vr, synth.blob_volume(n, synth.draw_blobs(rng, 2)), dict(kind="grid", grid=(43, 1, 3)),
+                   tf, lo, hi, cam)
+    assert e.value.status == vr.VR_ERR_ARG
+
+
 # --------------------------------------------------------------------------
 # brick packing, host output, errors
 # --------------------------------------------------------------------------
