@@ -451,8 +451,8 @@ def run_ours(a):
         ray_state_cycling=cyc,
         cpu_baseline=cpu,
         e2e=dict(value=samples / e2e_s, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=W * H * 16,
-                 note="vr_render_frame into pinned host memory: render + 33 MB device-to-host copy + wait "
-                      "per frame; the per-step host inputs are the camera (kernel parameters)"),
+                 note="vr_render_frame into pinned host memory: render + %.1f MB device-to-host copy + wait "
+                      "per frame; the per-step host inputs are the camera (kernel parameters)" % (W * H * 16 / 1e6)),
     )
     print(json.dumps(line))
 
