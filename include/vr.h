@@ -94,7 +94,8 @@ typedef struct {
  *   VR_PART_BOXES: n_bricks half-open voxel boxes (lo x,y,z, hi x,y,z) that
  *                  tile the volume and can be separated by axis-aligned cuts
  *                  (needed for a visibility order); otherwise VR_ERR_ARG.
- * At most VR_MAX_BRICKS bricks. */
+ * At most VR_MAX_BRICKS bricks. vr_volume_create also refuses (VR_ERR_ARG) a brick
+ * whose haloed storage exceeds 2^31 - 1 xy-quads (about 1290^3 voxels). */
 #define VR_MAX_BRICKS 128
 typedef struct {
     int kind;

@@ -790,6 +790,10 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
     const char *why = nullptr;
     if (!partition_plan(dims, part, vol->boxes, vol->tree, &why)) return fail(ctx, VR_ERR_ARG, why);
     const int nb = static_cast<int>(vol->boxes.size() / 6);
+    // quad indices inside a brick are 32-bit
+    for (int b = 0; b < nb; ++b)
+        if (brick_quads(&vol->boxes[6 * b]) > 0x7fffffffLL)
+            return fail(ctx, VR_ERR_ARG, "a brick holds more than 2^31 - 1 quads (about 1290^3 voxels); use more bricks");
 
     // brick-major haloed xy-quad storage, each brick 256-byte aligned
     const size_t es = quad_size(storage);
