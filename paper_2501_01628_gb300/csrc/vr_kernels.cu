@@ -54,6 +54,10 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     // transfer-function pairs (8 KB for 256 entries) are read through L1: one
     // cached copy per SM instead of one shared-memory copy per block
 
+    // the composite launched after this march may start (and compact its tile
+    // lists) once every block of this grid is running; it reads the partials
+    // only after this grid has completed
+    asm volatile("griddepcontrol.launch_dependents;");
     const int item = blockIdx.x;
     const int bi = find_brick(p, item);
     const BrickLaunch &B = p.b[bi];
@@ -157,6 +161,10 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
             }
     }
     __syncthreads();
+    // launched as a programmatic dependent of the march: wait here for the
+    // preceding grid's completion and memory (the tile list above reads only
+    // kernel parameters)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int m = s_m;
     const int px = tx0 + threadIdx.x;
     for (int half = 0; half < kCompRows; ++half) {
@@ -272,10 +280,23 @@ cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s)
     dim3 block(kCompW, kCompH);
     dim3 grid((p.W + kCompW - 1) / kCompW, (p.H + kCompH * kCompRows - 1) / (kCompH * kCompRows));
     if (p.W <= 0 || p.H <= 0) return cudaSuccess;
-    if (p.n_levels <= 1) composite_kernel<1><<<grid, block, 0, s>>>(p);
-    else if (p.n_levels <= 4) composite_kernel<4><<<grid, block, 0, s>>>(p);
-    else composite_kernel<kMaxFactors><<<grid, block, 0, s>>>(p);
-    return cudaGetLastError();
+    // programmatic dependent launch: the composite's blocks may start while the
+    // preceding kernel in the stream finishes (they wait in griddepcontrol.wait
+    // before touching its output); after any other stream operation, or a kernel
+    // that never signals, this is ordinary stream order
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (p.n_levels <= 1) return cudaLaunchKernelEx(&cfg, composite_kernel<1>, p);
+    if (p.n_levels <= 4) return cudaLaunchKernelEx(&cfg, composite_kernel<4>, p);
+    return cudaLaunchKernelEx(&cfg, composite_kernel<kMaxFactors>, p);
 }
 
 }  // namespace vr
