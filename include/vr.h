@@ -209,7 +209,10 @@ vr_status vr_set_count_samples(vr_ctx ctx, int on);
 vr_status vr_get_sample_count(vr_ctx ctx, long long *count);
 
 /* When on, the library records a CUDA event pair on the launching stream
- * around each of its march and composite kernel launches. Off by default. */
+ * around each of its march and composite kernel launches. Off by default.
+ * The events cost time (about 10 us per 1080p frame on a GB300) and keep the
+ * composite from starting in the march's tail, so switch timing on for a
+ * subset of frames when measuring throughput. */
 vr_status vr_set_kernel_timing(vr_ctx ctx, int on);
 /* Summed device time (ms) and launch count of the march and composite kernels
  * recorded since the last call (waits for the recorded events). Any output may
