@@ -76,24 +76,34 @@ def reduce_job(ms: float, e2e_s: float, samples: float, world: int, device: str 
     return float(mx[0]), float(mx[1]), float(sm[0])
 
 
+def source_key(sources) -> str:
+    """First 16 hex digits of the sha256 of the kernel sources with comments and
+    whitespace removed (a recorded measurement stays valid across comment edits)."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2501_01628_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sources:
+        text = open(os.path.join(csrc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(re.sub(r"\s+", "", text).encode())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(summary: str = "march_paper_workload.md",
                      sources=("vr_kernels.cu", "vr_device.cuh", "vr_internal.h")):
     """DRAM bytes per launch of a kernel from its committed ncu summary, if the
-    summary was taken on the current kernel source (else None)."""
-    import hashlib
+    summary was taken on the current kernel code (else None)."""
     import re
-    path = os.path.join(ROOT, "profiles", summary)
-    csrc = os.path.join(ROOT, "paper_2501_01628_gb300", "csrc")
     try:
-        text = open(path).read()
-        h = hashlib.sha256()
-        for f in sources:
-            h.update(open(os.path.join(csrc, f), "rb").read())
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        key = source_key(sources)
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    k = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    if not m or not k or k.group(1) != h.hexdigest()[:16]:
+    k = re.search(r"kernel_source_key:\s*([0-9a-f]+)", text)
+    if not m or not k or k.group(1) != key:
         return None
     return float(m.group(1))
 

@@ -45,15 +45,14 @@ __global__ void pack_kernel(PackParams p)
 }
 
 // ---------------------------------------------------------------------------
-// March: one thread per pixel of a brick's footprint; 8x4-pixel warp packets.
+// March: one thread per pixel of a brick's footprint. A block is a tile of
+// 2x2 warp packets of pw x (32/pw) pixels (pw = p.pw: 4, 8 or 16). The transfer
+// function is read as (T[i], T[i+1]-T[i]) pairs (the last difference is 0)
+// through L1: one cached copy per SM instead of one shared-memory copy per block.
 // ---------------------------------------------------------------------------
 template <typename S, bool COUNT, bool OPC>
 __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ MarchParams p)
 {
-    // transfer function as (T[i], T[i+1]-T[i]) pairs; the last difference is 0
-    // transfer-function pairs (8 KB for 256 entries) are read through L1: one
-    // cached copy per SM instead of one shared-memory copy per block
-
     // the composite launched after this march may start (and compact its tile
     // lists) once every block of this grid is running; it reads the partials
     // only after this grid has completed
