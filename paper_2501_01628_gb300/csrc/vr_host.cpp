@@ -319,20 +319,27 @@ cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
 {
     const size_t es = quad_size(vol->dtype);
     const int nb = static_cast<int>(vol->boxes.size() / 6);
-    cudaError_t e = cudaSuccess;
-    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+    static thread_local PackParams pp;
+    pp.src = dsrc;
+    for (int a = 0; a < 3; ++a) pp.N[a] = vol->dims[a];
+    pp.nb = nb;
+    long long blocks = 0;
+    for (int b = 0; b < nb; ++b) {
         const int *bx = &vol->boxes[6 * b];
-        PackParams pp;
-        pp.src = dsrc;
-        pp.dst = static_cast<char *>(vol->d_data) + vol->base[b] * static_cast<long long>(es);
+        PackBrick &B = pp.b[b];
+        B.dst = static_cast<char *>(vol->d_data) + vol->base[b] * static_cast<long long>(es);
+        B.quads = brick_quads(bx);
         for (int a = 0; a < 3; ++a) {
-            pp.N[a] = vol->dims[a];
-            pp.lo[a] = bx[a];
-            pp.s[a] = bx[3 + a] - bx[a] + 2;
+            B.lo[a] = bx[a];
+            B.s[a] = bx[3 + a] - bx[a] + 2;
         }
-        e = launch_pack(pp, vol->dtype, s);
+        B.block_begin = static_cast<int>(blocks);
+        B.pad = 0;
+        blocks += (B.quads + kPackChunk - 1) / kPackChunk;
     }
-    return e;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    pp.n_blocks = static_cast<int>(blocks);
+    return launch_pack(pp, vol->dtype, s);
 }
 
 vr_status ensure_frame(vr_ctx ctx, vr_frame_s &fr, long long px)

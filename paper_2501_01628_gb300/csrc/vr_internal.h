@@ -161,12 +161,24 @@ struct BatchParams {
     int wait_limit;                  // spin iterations (about 128 ns each) before giving up
 };
 
+// Pack of all bricks of a volume in one launch: block j of brick b (counted
+// from that brick's block_begin) writes the brick's storage quads
+// [j*kPackChunk, (j+1)*kPackChunk), in storage order.
+constexpr int kPackChunk = 2048;
+struct PackBrick {
+    void *dst;             // the brick's storage
+    long long quads;       // quads in the brick's storage (whole 2x2x2 blocks)
+    int lo[3];             // voxel box origin
+    int s[3];              // haloed extents (the brick stores (s0-1)(s1-1)s2 quads)
+    int block_begin;       // first block of this brick
+    int pad;
+};
 struct PackParams {
-    const float *src;
-    void *dst;
+    const float *src;      // x-fastest float32 volume
     int N[3];
-    int lo[3];
-    int s[3];       // haloed extents (the brick stores (s0-1)(s1-1)s2 quads)
+    int nb;
+    int n_blocks;
+    PackBrick b[kMaxBricks];
 };
 
 // Launchers (vr_kernels.cu). They return the launch's cudaError_t.

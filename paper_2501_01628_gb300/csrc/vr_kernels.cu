@@ -15,32 +15,48 @@ using dev::find_brick;
 using dev::over;
 
 // ---------------------------------------------------------------------------
-// Pack: global x-fastest float32 volume -> one brick of xy-quads (halo of one
+// Pack: global x-fastest float32 volume -> every brick's xy-quads (halo of one
 // voxel, edge-clamped), converted to the storage type with round-to-nearest.
+// One launch for all bricks; a block writes kPackChunk consecutive quads of one
+// brick's storage (2x2x2 blocks of quads, blocks x-fastest), so a warp's writes
+// are contiguous. Quads of the padding that rounds a brick's storage up to
+// whole blocks are not written.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void pack_kernel(PackParams p)
+__global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ PackParams p)
 {
+    int lo = 0, hi = p.nb - 1;  // the block's brick (the same for all its threads)
+    const int blk = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.b[mid].block_begin <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const PackBrick &B = p.b[lo];
     using Q = typename Quad<T>::type;
-    Q *dst = static_cast<Q *>(p.dst);
-    const int qx = p.s[0] - 1, qy = p.s[1] - 1, nbx = p.s[0] / 2, nby = p.s[1] / 2;
-    const long long qxy = static_cast<long long>(qx) * qy;
-    const long long count = qxy * p.s[2];
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < count;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int lz = static_cast<int>(e / qxy);
-        const long long rem = e - lz * qxy;
-        const int ly = static_cast<int>(rem / qx);
-        const int lx = static_cast<int>(rem - static_cast<long long>(ly) * qx);
-        const int gx0 = min(max(p.lo[0] + lx - 1, 0), p.N[0] - 1);
-        const int gx1 = min(max(p.lo[0] + lx, 0), p.N[0] - 1);
-        const int gy0 = min(max(p.lo[1] + ly - 1, 0), p.N[1] - 1);
-        const int gy1 = min(max(p.lo[1] + ly, 0), p.N[1] - 1);
-        const int gz = min(max(p.lo[2] + lz - 1, 0), p.N[2] - 1);
+    Q *dst = static_cast<Q *>(B.dst);
+    const int qx = B.s[0] - 1, qy = B.s[1] - 1, nbx = B.s[0] / 2, nby = B.s[1] / 2;
+    const long long q0 = static_cast<long long>(blk - B.block_begin) * kPackChunk;
+    const long long q1 = min(q0 + kPackChunk, B.quads);
+    for (long long q = q0 + threadIdx.x; q < q1; q += 256) {
+        // inverse of quad_index
+        const long long bl = q >> 3;
+        const int bx = static_cast<int>(bl % nbx);
+        const long long rest = bl / nbx;
+        const int by = static_cast<int>(rest % nby);
+        const int bz = static_cast<int>(rest / nby);
+        const int lx = 2 * bx + static_cast<int>(q & 1), ly = 2 * by + static_cast<int>((q >> 1) & 1);
+        const int lz = 2 * bz + static_cast<int>((q >> 2) & 1);
+        if (lx >= qx || ly >= qy || lz >= B.s[2]) continue;
+        const int gx0 = min(max(B.lo[0] + lx - 1, 0), p.N[0] - 1);
+        const int gx1 = min(max(B.lo[0] + lx, 0), p.N[0] - 1);
+        const int gy0 = min(max(B.lo[1] + ly - 1, 0), p.N[1] - 1);
+        const int gy1 = min(max(B.lo[1] + ly, 0), p.N[1] - 1);
+        const int gz = min(max(B.lo[2] + lz - 1, 0), p.N[2] - 1);
         const float *plane = p.src + static_cast<long long>(gz) * p.N[1] * p.N[0];
         const float *r0 = plane + static_cast<long long>(gy0) * p.N[0];
         const float *r1 = plane + static_cast<long long>(gy1) * p.N[0];
-        dst[quad_index(lx, ly, lz, nbx, nby)] = Quad<T>::make(r0[gx0], r0[gx1], r1[gx0], r1[gx1]);
+        dst[q] = Quad<T>::make(__ldg(r0 + gx0), __ldg(r0 + gx1), __ldg(r1 + gx0), __ldg(r1 + gx1));
     }
 }
 
@@ -219,15 +235,11 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s)
 {
-    const long long count = static_cast<long long>(p.s[0] - 1) * (p.s[1] - 1) * p.s[2];
-    if (count <= 0) return cudaSuccess;
-    const int threads = 256;
-    long long blocks = (count + threads - 1) / threads;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (p.n_blocks <= 0) return cudaSuccess;
     switch (dtype) {
-    case VR_F32: pack_kernel<float><<<static_cast<int>(blocks), threads, 0, s>>>(p); break;
-    case VR_BF16: pack_kernel<__nv_bfloat16><<<static_cast<int>(blocks), threads, 0, s>>>(p); break;
-    case VR_F16: pack_kernel<__half><<<static_cast<int>(blocks), threads, 0, s>>>(p); break;
+    case VR_F32: pack_kernel<float><<<p.n_blocks, 256, 0, s>>>(p); break;
+    case VR_BF16: pack_kernel<__nv_bfloat16><<<p.n_blocks, 256, 0, s>>>(p); break;
+    case VR_F16: pack_kernel<__half><<<p.n_blocks, 256, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
