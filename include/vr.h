@@ -345,6 +345,22 @@ vr_status vr_mesh_info(vr_mesh mesh, int *n_bricks, long long *elements_per_bric
  * on `stream` like vr_render_frame. VR_ERR_STATE in ray-state cycling mode. */
 vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int out_on_device, void *stream);
 
+/* ---- fault injection (test hook) ----------------------------------------- */
+
+/* For testing the error paths of the library and of its callers; the paper has
+ * no counterpart. After `after` further successful device allocations (kind
+ * VR_FAULT_ALLOC) or kernel launches (kind VR_FAULT_LAUNCH) made by the library
+ * in this process, the next one fails on the host without calling CUDA: the
+ * call in progress returns VR_ERR_OOM or VR_ERR_CUDA with a message naming the
+ * injected fault, and the context and its objects stay usable. The plan is
+ * one-shot and process-wide; VR_FAULT_NONE clears it. No GPU fault is raised:
+ * nothing is launched or allocated in place of the failed operation.
+ * VR_ERR_ARG for an unknown kind or a negative count. */
+#define VR_FAULT_NONE 0
+#define VR_FAULT_ALLOC 1
+#define VR_FAULT_LAUNCH 2
+vr_status vr_debug_inject_fault(int kind, int after);
+
 /* ---- rendering without device allocation -------------------------------- */
 
 /* The paper has no counterpart to this call; it exists for callers that must

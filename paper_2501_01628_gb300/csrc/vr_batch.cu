@@ -394,17 +394,17 @@ vr_status build(vr_batch b, int pw, int bps, int mode)
         begin[g + 1] = begin[g] + m + c;
     }
     DeviceGuard g(ctx->device);
-    VR_CUDA(ctx, cudaMalloc(&b->d_views, views.size() * sizeof(BatchView)));
-    VR_CUDA(ctx, cudaMalloc(&b->d_vb, vb.size() * sizeof(BrickLaunch)));
-    VR_CUDA(ctx, cudaMalloc(&b->d_order, order.size() * sizeof(int)));
-    VR_CUDA(ctx, cudaMalloc(&b->d_render_begin, begin.size() * sizeof(long long)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&b->d_views, views.size() * sizeof(BatchView)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&b->d_vb, vb.size() * sizeof(BrickLaunch)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&b->d_order, order.size() * sizeof(int)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&b->d_render_begin, begin.size() * sizeof(long long)));
     VR_CUDA(ctx, cudaMemcpy(b->d_views, views.data(), views.size() * sizeof(BatchView), cudaMemcpyHostToDevice));
     VR_CUDA(ctx, cudaMemcpy(b->d_vb, vb.data(), vb.size() * sizeof(BrickLaunch), cudaMemcpyHostToDevice));
     VR_CUDA(ctx, cudaMemcpy(b->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
     VR_CUDA(ctx, cudaMemcpy(b->d_render_begin, begin.data(), begin.size() * sizeof(long long), cudaMemcpyHostToDevice));
-    VR_CUDA(ctx, cudaMalloc(&b->d_unit_march, unit_march.size() * sizeof(int)));
-    VR_CUDA(ctx, cudaMalloc(&b->d_unit_comp, unit_comp.size() * sizeof(int)));
-    VR_CUDA(ctx, cudaMalloc(&b->d_bw_begin, bw.size() * sizeof(long long)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&b->d_unit_march, unit_march.size() * sizeof(int)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&b->d_unit_comp, unit_comp.size() * sizeof(int)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&b->d_bw_begin, bw.size() * sizeof(long long)));
     VR_CUDA(ctx, cudaMemcpy(b->d_unit_march, unit_march.data(), unit_march.size() * sizeof(int), cudaMemcpyHostToDevice));
     VR_CUDA(ctx, cudaMemcpy(b->d_unit_comp, unit_comp.data(), unit_comp.size() * sizeof(int), cudaMemcpyHostToDevice));
     VR_CUDA(ctx, cudaMemcpy(b->d_bw_begin, bw.data(), bw.size() * sizeof(long long), cudaMemcpyHostToDevice));
@@ -417,7 +417,7 @@ vr_status build(vr_batch b, int pw, int bps, int mode)
         cudaFree(b->d_ring);
         b->d_ring = nullptr;
         b->ring_px = 0;
-        VR_CUDA(ctx, cudaMalloc(&b->d_ring, static_cast<size_t>(need) * sizeof(float4)));
+        VR_CUDA(ctx, vr::host::dev_malloc(&b->d_ring, static_cast<size_t>(need) * sizeof(float4)));
         b->ring_px = need;
     }
     int sms = 0;
@@ -465,6 +465,7 @@ vr_status build(vr_batch b, int pw, int bps, int mode)
     cudaError_t e = cudaMemsetAsync(b->d_claim, 0, sizeof(unsigned long long), b->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_march_done, 0, nu * sizeof(int), b->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_comp_done, 0, nu * sizeof(int), b->cap);
+    if (e == cudaSuccess && vr::host::fault_now(VR_FAULT_LAUNCH)) e = cudaErrorLaunchFailure;
     if (e == cudaSuccess) e = launch_batch(p, b->dtype, sms * bps, b->cap);
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
@@ -524,11 +525,11 @@ vr_status vr_batch_create(vr_ctx ctx, int n_volumes, const vr_volume *vols, cons
     std::vector<const void *> data(n_volumes);
     for (int i = 0; i < n_volumes; ++i) data[i] = vols[i]->d_data;
     const int nr = n_volumes * n_views;
-    cudaError_t e = cudaMalloc(&b->d_vol_data, n_volumes * sizeof(void *));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_vol_tf, n_volumes * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_claim, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_march_done, nr * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_comp_done, nr * sizeof(int));
+    cudaError_t e = vr::host::dev_malloc(&b->d_vol_data, n_volumes * sizeof(void *));
+    if (e == cudaSuccess) e = vr::host::dev_malloc(&b->d_vol_tf, n_volumes * sizeof(float2));
+    if (e == cudaSuccess) e = vr::host::dev_malloc(&b->d_claim, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = vr::host::dev_malloc(&b->d_march_done, nr * sizeof(int));
+    if (e == cudaSuccess) e = vr::host::dev_malloc(&b->d_comp_done, nr * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_vol_data, data.data(), n_volumes * sizeof(void *), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_vol_tf, b->vol_tf.data(), n_volumes * sizeof(float2), cudaMemcpyHostToDevice);
@@ -547,6 +548,7 @@ vr_status vr_batch_create(vr_ctx ctx, int n_volumes, const vr_volume *vols, cons
 
 vr_status vr_batch_launch(vr_batch b, void *stream)
 {
+    vr::host::TraceRange trace_("vr_batch_launch");
     if (!b || !b->exec) return VR_ERR_ARG;
     DeviceGuard g(b->ctx->device);
     VR_CUDA(b->ctx, cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));

@@ -7,6 +7,7 @@
 // Sec. 3: rendering is one collective call whose image ends up in one
 // framebuffer; the world is distributed and updated locally.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -22,6 +23,18 @@ using namespace vr::host;
 
 namespace vr {
 namespace host {
+
+// ---- fault injection (vr_debug_inject_fault) --------------------------------
+std::atomic<int> g_fault_kind{VR_FAULT_NONE};
+std::atomic<long long> g_fault_after{0};
+
+bool fault_now(int kind)
+{
+    if (g_fault_kind.load(std::memory_order_relaxed) != kind) return false;
+    if (g_fault_after.fetch_sub(1) > 0) return false;
+    g_fault_kind.store(VR_FAULT_NONE);
+    return true;
+}
 
 size_t elem_size(vr_dtype t) { return t == VR_F32 ? 4 : 2; }
 // bytes of one xy-quad (four voxels) in device storage
@@ -339,6 +352,7 @@ cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
     }
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     pp.n_blocks = static_cast<int>(blocks);
+    if (fault_now(VR_FAULT_LAUNCH)) return cudaErrorLaunchFailure;
     return launch_pack(pp, vol->dtype, s);
 }
 
@@ -349,7 +363,7 @@ vr_status ensure_frame(vr_ctx ctx, vr_frame_s &fr, long long px)
     if (fr.d_part) cudaFree(fr.d_part);
     fr.d_part = nullptr;
     fr.cap_px = 0;
-    VR_CUDA(ctx, cudaMalloc(&fr.d_part, static_cast<size_t>(want) * sizeof(float4)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&fr.d_part, static_cast<size_t>(want) * sizeof(float4)));
     fr.cap_px = want;
     return VR_OK;
 }
@@ -481,7 +495,7 @@ vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s)
     if (st != VR_OK) return st;
     mp.partials = fr.d_part;
     const int t = timing_begin(ctx, 0, s);
-    VR_CUDA(ctx, launch_march(mp, vol->dtype, s));
+    VR_LAUNCH(ctx, launch_march(mp, vol->dtype, s));
     timing_end(ctx, t, s);
     return VR_OK;
 }
@@ -519,7 +533,7 @@ vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s)
     cp.partials = fr.d_part;
     cp.out = out;
     const int t = timing_begin(ctx, 1, s);
-    VR_CUDA(ctx, launch_composite(cp, s));
+    VR_LAUNCH(ctx, launch_composite(cp, s));
     timing_end(ctx, t, s);
     return VR_OK;
 }
@@ -534,7 +548,7 @@ vr_status host_staging(vr_ctx ctx, long long px, cudaStream_t s, float4 **buf, i
             if (ctx->d_img) cudaFree(ctx->d_img);
             ctx->d_img = nullptr;
             ctx->img_cap = 0;
-            VR_CUDA(ctx, cudaMalloc(&ctx->d_img, static_cast<size_t>(px) * sizeof(float4)));
+            VR_CUDA(ctx, vr::host::dev_malloc(&ctx->d_img, static_cast<size_t>(px) * sizeof(float4)));
             ctx->img_cap = px;
         }
         *buf = ctx->d_img;
@@ -556,7 +570,7 @@ vr_status host_staging(vr_ctx ctx, long long px, cudaStream_t s, float4 **buf, i
         }
         ctx->img2_cap = 0;
         for (int i = 0; i < 2; ++i)
-            VR_CUDA(ctx, cudaMalloc(&ctx->d_img2[i], static_cast<size_t>(px) * sizeof(float4)));
+            VR_CUDA(ctx, vr::host::dev_malloc(&ctx->d_img2[i], static_cast<size_t>(px) * sizeof(float4)));
         ctx->img2_cap = px;
     }
     const int k = ctx->img_next;
@@ -613,7 +627,7 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
         if (st != VR_OK) return st;
     }
     const int t = timing_begin(ctx, 0, s);
-    VR_CUDA(ctx, launch_march_cycle(mp, vol->dtype, dst, s));
+    VR_LAUNCH(ctx, launch_march_cycle(mp, vol->dtype, dst, s));
     timing_end(ctx, t, s);
     if (!out_on_device) return host_copy(ctx, out, dst, slot, px, s);
     return VR_OK;
@@ -687,9 +701,9 @@ vr_status vr_create(int cuda_device, vr_ctx *out)
     if (!ctx) return VR_ERR_OOM;
     ctx->device = cuda_device;
     DeviceGuard g(cuda_device);
-    if (!g.ok || cudaMalloc(&ctx->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
+    if (!g.ok || vr::host::dev_malloc(&ctx->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(ctx->d_counter, 0, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&ctx->d_error, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_error, 0, sizeof(int)) != cudaSuccess) {
+        vr::host::dev_malloc(&ctx->d_error, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_error, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(ctx->d_counter);
         cudaFree(ctx->d_error);
@@ -784,6 +798,7 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
 vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, const vr_partition *part,
                            const float *src, int src_on_device, void *stream, vr_volume *out)
 {
+    vr::host::TraceRange trace_("vr_volume_create");
     if (!ctx || !out) return VR_ERR_ARG;
     *out = nullptr;
     if (!dims || !part || !src) return fail(ctx, VR_ERR_ARG, "null argument");
@@ -813,13 +828,13 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
     }
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    VR_CUDA(ctx, cudaMalloc(&vol->d_data, static_cast<size_t>(off_bytes)));
+    VR_CUDA(ctx, vr::host::dev_malloc(&vol->d_data, static_cast<size_t>(off_bytes)));
     vol->bytes = off_bytes;
     const float *dsrc = src;
     float *tmp = nullptr;
     const size_t nvox = static_cast<size_t>(dims[0]) * dims[1] * dims[2];
     if (!src_on_device) {
-        cudaError_t e = cudaMalloc(&tmp, nvox * sizeof(float));
+        cudaError_t e = vr::host::dev_malloc(&tmp, nvox * sizeof(float));
         if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, nvox * sizeof(float), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) {
             cudaFree(tmp);
@@ -842,6 +857,7 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
 
 vr_status vr_volume_update(vr_volume vol, const float *src, int src_on_device, void *stream)
 {
+    vr::host::TraceRange trace_("vr_volume_update");
     if (!vol || !src) return VR_ERR_ARG;
     vr_ctx ctx = vol->ctx;
     DeviceGuard g(ctx->device);
@@ -850,7 +866,7 @@ vr_status vr_volume_update(vr_volume vol, const float *src, int src_on_device, v
     const float *dsrc = src;
     float *tmp = nullptr;
     if (!src_on_device) {
-        VR_CUDA(ctx, cudaMalloc(&tmp, nvox * sizeof(float)));
+        VR_CUDA(ctx, vr::host::dev_malloc(&tmp, nvox * sizeof(float)));
         cudaError_t e = cudaMemcpyAsync(tmp, src, nvox * sizeof(float), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) {
             cudaFree(tmp);
@@ -867,6 +883,7 @@ vr_status vr_volume_update(vr_volume vol, const float *src, int src_on_device, v
 
 vr_status vr_volume_update_async(vr_volume vol, const float *src, int src_on_device, void *stream)
 {
+    vr::host::TraceRange trace_("vr_volume_update_async");
     if (!vol || !src) return VR_ERR_ARG;
     vr_ctx ctx = vol->ctx;
     DeviceGuard g(ctx->device);
@@ -874,7 +891,7 @@ vr_status vr_volume_update_async(vr_volume vol, const float *src, int src_on_dev
     const size_t nvox = static_cast<size_t>(vol->dims[0]) * vol->dims[1] * vol->dims[2];
     const float *dsrc = src;
     if (!src_on_device) {
-        if (!vol->d_staging) VR_CUDA(ctx, cudaMalloc(&vol->d_staging, nvox * sizeof(float)));
+        if (!vol->d_staging) VR_CUDA(ctx, vr::host::dev_malloc(&vol->d_staging, nvox * sizeof(float)));
         VR_CUDA(ctx, cudaMemcpyAsync(vol->d_staging, src, nvox * sizeof(float), cudaMemcpyHostToDevice, s));
         dsrc = vol->d_staging;
     }
@@ -885,6 +902,7 @@ vr_status vr_volume_update_async(vr_volume vol, const float *src, int src_on_dev
 vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_dev, float *grad_tf_dev,
                              float *grad_density_dev, void *stream)
 {
+    vr::host::TraceRange trace_("vr_render_backward");
     if (!ctx || !vol) return VR_ERR_ARG;
     if (!grad_rgba_dev || !grad_tf_dev) return fail(ctx, VR_ERR_ARG, "null gradient buffer");
     if (vol->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume belongs to another context");
@@ -901,12 +919,12 @@ vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_d
     if (st != VR_OK) return st;
     mp.partials = fr.d_part;
     mp.sample_counter = nullptr;
-    VR_CUDA(ctx, launch_march(mp, vol->dtype, s));
+    VR_LAUNCH(ctx, launch_march(mp, vol->dtype, s));
     if (fr.total_px > ctx->gpart_cap) {
         cudaFree(ctx->d_gpart);
         ctx->d_gpart = nullptr;
         ctx->gpart_cap = 0;
-        VR_CUDA(ctx, cudaMalloc(&ctx->d_gpart, static_cast<size_t>(fr.total_px) * sizeof(float4)));
+        VR_CUDA(ctx, vr::host::dev_malloc(&ctx->d_gpart, static_cast<size_t>(fr.total_px) * sizeof(float4)));
         ctx->gpart_cap = fr.total_px;
     }
     static thread_local CompositeGradParams cg;
@@ -922,14 +940,14 @@ vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_d
     cg.partials = fr.d_part;
     cg.grad_img = reinterpret_cast<const float4 *>(grad_rgba_dev);
     cg.grad_partials = ctx->d_gpart;
-    VR_CUDA(ctx, launch_composite_grad(cg, s));
+    VR_LAUNCH(ctx, launch_composite_grad(cg, s));
     GradArgs ga;
     ga.grad_partials = ctx->d_gpart;
     ga.grad_tf = grad_tf_dev;
     ga.grad_vol = grad_density_dev;
     for (int a = 0; a < 3; ++a) ga.N[a] = vol->dims[a];
     ga.error = ctx->d_error;
-    VR_CUDA(ctx, launch_march_grad(mp, ga, vol->dtype, s));
+    VR_LAUNCH(ctx, launch_march_grad(mp, ga, vol->dtype, s));
     return VR_OK;
 }
 
@@ -995,7 +1013,7 @@ vr_status vr_set_transfer_function(vr_ctx ctx, const float *rgba, int n, float v
         ctx->d_tf = nullptr;
         ctx->tf_cap = 0;
         ctx->has_tf = false;
-        VR_CUDA(ctx, cudaMalloc(&ctx->d_tf, 2 * static_cast<size_t>(n) * sizeof(float4)));
+        VR_CUDA(ctx, vr::host::dev_malloc(&ctx->d_tf, 2 * static_cast<size_t>(n) * sizeof(float4)));
         ctx->tf_cap = n;
     }
     // device table: (T[i], T[i+1] - T[i]) pairs in float32, last difference 0
@@ -1069,6 +1087,7 @@ vr_status vr_get_sample_count(vr_ctx ctx, long long *count)
 
 vr_status vr_render_partials(vr_ctx ctx, vr_volume vol, vr_frame *out, void *stream)
 {
+    vr::host::TraceRange trace_("vr_render_partials");
     if (!ctx || !vol || !out) return VR_ERR_ARG;
     *out = nullptr;
     if (vol->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume belongs to another context");
@@ -1103,6 +1122,7 @@ vr_status vr_frame_partial(vr_frame fr, int brick, const float **dev_ptr)
 
 vr_status vr_composite(vr_ctx ctx, vr_frame fr, float *out_rgba, int out_on_device, void *stream)
 {
+    vr::host::TraceRange trace_("vr_composite");
     if (!ctx || !fr) return VR_ERR_ARG;
     if (fr->ctx != ctx) return fail(ctx, VR_ERR_ARG, "frame belongs to another context");
     DeviceGuard g(ctx->device);
@@ -1121,6 +1141,7 @@ vr_status vr_frame_release(vr_frame fr)
 
 vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on_device, void *stream)
 {
+    vr::host::TraceRange trace_("vr_render_frame");
     if (!ctx || !vol) return VR_ERR_ARG;
     if (vol->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume belongs to another context");
     DeviceGuard g(ctx->device);
@@ -1165,3 +1186,12 @@ vr_status vr_set_render_mode(vr_ctx ctx, int mode)
 }
 
 }  // extern "C"
+
+vr_status vr_debug_inject_fault(int kind, int after)
+{
+    if (kind < VR_FAULT_NONE || kind > VR_FAULT_LAUNCH || after < 0) return VR_ERR_ARG;
+    g_fault_kind.store(VR_FAULT_NONE);
+    g_fault_after.store(after);
+    g_fault_kind.store(kind);
+    return VR_OK;
+}

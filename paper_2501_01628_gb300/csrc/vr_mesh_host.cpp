@@ -259,6 +259,7 @@ extern "C" {
 vr_status vr_mesh_create(vr_ctx ctx, const int dims[3], const vr_partition *part, const float *verts,
                          long long n_verts, const float *values, const int *tets, long long n_tets, vr_mesh *out)
 {
+    vr::host::TraceRange trace_("vr_mesh_create");
     if (!ctx || !out) return VR_ERR_ARG;
     *out = nullptr;
     if (!dims || !part || !verts || !values || !tets) return fail(ctx, VR_ERR_ARG, "null argument");
@@ -343,9 +344,9 @@ vr_status vr_mesh_create(vr_ctx ctx, const int dims[3], const vr_partition *part
         cudaFree(m->d_nbr);
         cudaFree(m->d_nodes);
     };
-    cudaError_t e = cudaMalloc(&m->d_rec, rec_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_nbr, nbr_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_nodes, node_bytes);
+    cudaError_t e = vr::host::dev_malloc(&m->d_rec, rec_bytes);
+    if (e == cudaSuccess) e = vr::host::dev_malloc(&m->d_nbr, nbr_bytes);
+    if (e == cudaSuccess) e = vr::host::dev_malloc(&m->d_nodes, node_bytes);
     for (int b = 0; e == cudaSuccess && b < nb; ++b) {
         const BrickBuild &B = bricks[b];
         e = cudaMemcpy(m->d_rec + kMeshRec * m->rec_base[b], B.rec.data(), B.rec.size() * sizeof(float4),
@@ -391,6 +392,7 @@ vr_status vr_mesh_info(vr_mesh mesh, int *n_bricks, long long *elements_per_bric
 
 vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int out_on_device, void *stream)
 {
+    vr::host::TraceRange trace_("vr_render_mesh_frame");
     if (!ctx || !mesh) return VR_ERR_ARG;
     if (mesh->ctx != ctx) return fail(ctx, VR_ERR_ARG, "mesh belongs to another context");
     if (!out_rgba) return fail(ctx, VR_ERR_ARG, "null output");
@@ -412,7 +414,7 @@ vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int ou
     }
     mp.error = ctx->d_error;
     const int t = timing_begin(ctx, 0, s);
-    VR_CUDA(ctx, launch_march_mesh(mp, s));
+    VR_LAUNCH(ctx, launch_march_mesh(mp, s));
     timing_end(ctx, t, s);
     return composite_to(ctx, ctx->frame, out_rgba, out_on_device, s);
 }

@@ -5,10 +5,36 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vr_internal.h"
 
 namespace vr {
 namespace host {
+
+// Fault injection for tests (vr_debug_inject_fault): a one-shot plan that makes
+// the device allocation or kernel launch after `after` successful ones fail on
+// the host, without calling CUDA.
+bool fault_now(int kind);  // kind: VR_FAULT_ALLOC or VR_FAULT_LAUNCH
+
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    if (fault_now(VR_FAULT_ALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+
+// Named NVTX range around a public call (visible in timeline profilers; a no-op
+// unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 struct KdNode {
     int axis = -1;  // -1: leaf
@@ -137,4 +163,12 @@ void timing_end(vr_ctx ctx, int idx, cudaStream_t s);
     do {                                                     \
         cudaError_t e_ = (call);                             \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// A kernel launch through a launcher, with the launch fault hook.
+#define VR_LAUNCH(ctx, call)                                                              \
+    do {                                                                                  \
+        if (vr::host::fault_now(VR_FAULT_LAUNCH))                                          \
+            return cuda_fail(ctx, cudaErrorLaunchFailure, #call " (injected fault)");     \
+        VR_CUDA(ctx, call);                                                               \
     } while (0)

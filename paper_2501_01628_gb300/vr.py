@@ -39,7 +39,7 @@ EXPORTS = (
     "vr_batch_autotune", "vr_batch_release", "vr_batch_configure", "vr_set_render_mode",
     "vr_set_opacity_correction", "vr_volume_update_async", "vr_set_packet_width",
     "vr_set_host_output_async", "vr_mesh_create", "vr_mesh_release", "vr_mesh_info",
-    "vr_render_mesh_frame",
+    "vr_render_mesh_frame", "vr_debug_inject_fault",
 )
 
 
@@ -86,6 +86,7 @@ _SIG = {
     "vr_frame_release": (_I, [_P]),
     "vr_render_frame": (_I, [_P, _P, _P, _I, _P]),
     "vr_set_kernel_timing": (_I, [_P, _I]),
+    "vr_debug_inject_fault": (_I, [_I, _I]),
     "vr_get_kernel_timing": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "vr_render_frame_noalloc": (_I, [_P, _P, ctypes.POINTER(vr_partition), _P, _I, ctypes.c_float,
@@ -404,6 +405,15 @@ def vr_get_sample_count(ctx) -> int:
     v = ctypes.c_longlong()
     _check(lib().vr_get_sample_count(ctx, ctypes.byref(v)), ctx, "vr_get_sample_count")
     return int(v.value)
+
+
+VR_FAULT_NONE, VR_FAULT_ALLOC, VR_FAULT_LAUNCH = 0, 1, 2
+
+
+def vr_debug_inject_fault(kind: int, after: int = 0):
+    """One-shot, process-wide: the device allocation (VR_FAULT_ALLOC) or kernel
+    launch (VR_FAULT_LAUNCH) after `after` successful ones fails on the host."""
+    _check(lib().vr_debug_inject_fault(int(kind), int(after)), None, "vr_debug_inject_fault")
 
 
 def vr_set_kernel_timing(ctx, on: bool):
