@@ -203,7 +203,10 @@ vr_status vr_set_packet_width(vr_ctx ctx, int packet_width);
  * sort-last steps. */
 vr_status vr_set_render_mode(vr_ctx ctx, int mode);
 /* When on, every march launch also counts executed samples (see
- * vr_get_sample_count). Off by default. */
+ * vr_get_sample_count). Off by default. The counting launches also check that
+ * every executed sample's quads lie inside its brick's storage (the index clamps
+ * of the march only guard memory); a violation makes the next vr_sync return
+ * VR_ERR_BOUNDS. */
 vr_status vr_set_count_samples(vr_ctx ctx, int on);
 /* Samples counted since the last call (synchronises the context's device). */
 vr_status vr_get_sample_count(vr_ctx ctx, long long *count);

@@ -263,7 +263,8 @@ template <typename S, bool COUNT, bool OPC = false>
 __device__ __forceinline__ void march_accumulate(const void *data, const BrickLaunch &B, const OwnedRun &run,
                                                  const float4 *tf, float tf_scale, float tf_bias, int ntf,
                                                  float ert_T, float &C0, float &C1, float &C2, float &T,
-                                                 unsigned long long &executed, float opc_ratio = 1.0f)
+                                                 unsigned long long &executed, float opc_ratio = 1.0f,
+                                                 int *count_error = nullptr)
 {
     const int ka = run.ka, kb = run.kb;
     if (ka > kb) return;
@@ -284,14 +285,18 @@ __device__ __forceinline__ void march_accumulate(const void *data, const BrickLa
     const unsigned long long st_z = f2_pack(run.step[2], run.step[2]), bs_z = f2_pack(run.base[2], run.base[2]);
     const unsigned long long tfs2 = f2_pack(tf_scale, tf_scale), tfb2 = f2_pack(tf_bias, tf_bias);
     // quad indices of the cell (plane k) and of plane k+1 from the floors' bits
-    auto cells = [&](unsigned bx, unsigned by, unsigned bz, unsigned &cell, unsigned &cell1) {
+    // the counting variant also checks the claim that the clamps only guard
+    // memory: an owned sample's quads must lie in the brick's storage
+    auto cells = [&](unsigned bx, unsigned by, unsigned bz, unsigned &cell, unsigned &cell1, bool owned) {
         unsigned c = bz * az + c0;
         c = by * ay + c;
         c = bx * 4u + c;
         c = (bx & 1u) * (0u - 3u) + c;
         c = (by & 1u) * py + c;
         c = (bz & 1u) * pz + c;
-        cell1 = min(c + 4u + (bz & 1u) * dz, last);
+        const unsigned c1 = c + 4u + (bz & 1u) * dz;
+        if (COUNT && owned && count_error && (c > last || c1 > last)) atomicOr(count_error, 16);
+        cell1 = min(c1, last);
         cell = min(c, last);
     };
     auto trilinear = [&](const float4 &a0, const float4 &a1, float wx, float wy, float wz) {
@@ -331,8 +336,8 @@ __device__ __forceinline__ void march_accumulate(const void *data, const BrickLa
         f2_unpack(yy, fya, fyb);
         f2_unpack(yz, fza, fzb);
         unsigned ca, ca1, cb, cb1;
-        cells(__float_as_uint(fxa), __float_as_uint(fya), __float_as_uint(fza), ca, ca1);
-        cells(__float_as_uint(fxb), __float_as_uint(fyb), __float_as_uint(fzb), cb, cb1);
+        cells(__float_as_uint(fxa), __float_as_uint(fya), __float_as_uint(fza), ca, ca1, true);
+        cells(__float_as_uint(fxb), __float_as_uint(fyb), __float_as_uint(fzb), cb, cb1, two);
         if (ca != prev) {
             q0 = Quad<S>::load(vox + ca);
             q1 = Quad<S>::load(vox + ca1);
@@ -373,11 +378,12 @@ __device__ __forceinline__ void march_accumulate(const void *data, const BrickLa
 template <typename S, bool COUNT, bool OPC = false>
 __device__ __forceinline__ float4 march_run(const void *data, const BrickLaunch &B, const OwnedRun &run,
                                             const float4 *tf, float tf_scale, float tf_bias, int ntf, float ert_T,
-                                            unsigned long long &executed, float opc_ratio = 1.0f)
+                                            unsigned long long &executed, float opc_ratio = 1.0f,
+                                            int *count_error = nullptr)
 {
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
     march_accumulate<S, COUNT, OPC>(data, B, run, tf, tf_scale, tf_bias, ntf, ert_T, C0, C1, C2, T, executed,
-                                    opc_ratio);
+                                    opc_ratio, count_error);
     return make_float4(C0, C1, C2, 1.0f - T);
 }
 

@@ -449,6 +449,7 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
     mp.tf = ctx->d_tf;
     mp.data = vol->d_data;
     mp.sample_counter = ctx->count_samples ? ctx->d_counter : nullptr;
+    mp.count_error = ctx->d_error;
     mp.nb = nb;
     mp.n_items = items;
     for (int j = 0; j < nb; ++j) mp.order[j] = fr.order[j];
@@ -790,6 +791,8 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
         VR_CUDA(ctx, cudaMemset(ctx->d_error, 0, sizeof(int)));
         if (err & 2) return fail(ctx, VR_ERR_TIMEOUT, "a bounded device-side wait of the batched kernel gave up");
         if (err & 8) return fail(ctx, VR_ERR_BOUNDS, "a mesh point location found no element");
+        if (err & 16)
+            return fail(ctx, VR_ERR_BOUNDS, "a counted sample's quad index fell outside its brick's storage");
         return fail(ctx, VR_ERR_BOUNDS, "a backward pass met an owned-sample run longer than 4096 samples");
     }
     return VR_OK;

@@ -70,6 +70,8 @@ struct MarchParams {
     const void *data;   // brick storage
     float4 *partials;   // partial pool
     unsigned long long *sample_counter;  // non-null: count executed samples
+    int *count_error;   // device error word; bit 4: in a counting launch, an executed
+                        // sample's quad index fell outside its brick's storage
     int nb;
     int n_items;
     int order[kMaxBricks];  // brick ids front to back (ray-state cycling)

@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     dev::OwnedRun run;
     dev::owned_run(p, B, px, py, run);
     const float4 c =
-        dev::march_run<S, COUNT, OPC>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, executed, p.opc_ratio);
+        dev::march_run<S, COUNT, OPC>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, executed, p.opc_ratio,
+                                      p.count_error);
     p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = c;
     if (COUNT && executed) atomicAdd(p.sample_counter, executed);
 }
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant_
         dev::OwnedRun run;
         dev::brick_run(p, B, ray, run);
         dev::march_accumulate<S, COUNT, OPC>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, C0, C1,
-                                             C2, T, executed, p.opc_ratio);
+                                             C2, T, executed, p.opc_ratio, p.count_error);
         if (T <= p.ert_T) break;
     }
     out[static_cast<long long>(py) * p.W + px] = make_float4(C0, C1, C2, 1.0f - T);

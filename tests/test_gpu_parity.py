@@ -83,7 +83,8 @@ def test_perspective_and_partition_variants(vr, case):
     tf = synth.random_tf(rng, alpha_max=0.15)
     lo, hi = synth.volume_range(vol)
     boxes = vr.vr_partition_boxes((n,) * 3, part)
-    got = gpu_render(vr, vol, part, tf, lo, hi, cam, step=step)
+    # counting launch: also checks that every executed sample's quads lie in its brick
+    got = gpu_render(vr, vol, part, tf, lo, hi, cam, step=step, count=True)
     env = oracle_env(vol, boxes, tf, lo, hi, cam, step)
     compare_envelope(got["img"], env)
 
@@ -160,7 +161,7 @@ def test_maximum_bricks_and_deepest_radix_tree(vr):
     part = dict(kind="grid", grid=(8, 4, 4))
     boxes = oracle.grid_partition((n,) * 3, (8, 4, 4))
     env = oracle_env(vol, boxes, tf, lo, hi, cam)
-    direct = gpu_render(vr, vol, part, tf, lo, hi, cam)["img"]
+    direct = gpu_render(vr, vol, part, tf, lo, hi, cam, count=True)["img"]
     compare_envelope(direct, env)
     for sched in ([2] * 7, [8, 16], [4, 4, 8]):
         got = gpu_render(vr, vol, part, tf, lo, hi, cam, schedule=sched)["img"]
@@ -191,7 +192,7 @@ def test_packet_widths_give_identical_images(vr, mode):
         tf = synth.random_tf(rng, alpha_max=0.2)
         lo, hi = synth.volume_range(vol)
         imgs = [gpu_render(vr, vol, part, tf, lo, hi, cam, step=step, ert=0.9, schedule=(),
-                           packet_width=pw, mode=mode)["img"] for pw in (4, 8, 16)]
+                           packet_width=pw, mode=mode, count=True)["img"] for pw in (4, 8, 16)]
         assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[0], imgs[2]), case
 
 
@@ -208,7 +209,7 @@ def test_paper_workload_sampled(vr):
     vol_dev = torch.from_numpy(vol).cuda()
     for k, az in enumerate((synth.ORBIT_AZIMUTHS[0], synth.ORBIT_AZIMUTHS[3])):
         cam = synth.orbit_camera(1920, 1080, az)
-        got = gpu_render(vr, vol_dev, part, tf, lo, hi, cam, 0.5, 0.99, schedule=(4, 3, 3))["img"]
+        got = gpu_render(vr, vol_dev, part, tf, lo, hi, cam, 0.5, 0.99, schedule=(4, 3, 3), count=True)["img"]
         prng = np.random.default_rng(30 + k)
         pix = np.stack([prng.integers(0, 1920, 2048), prng.integers(0, 1080, 2048)], axis=1)
         env = oracle_env(vol, boxes, tf, lo, hi, cam, 0.5, 0.99, pixels=pix)
