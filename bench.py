@@ -187,6 +187,29 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 
 
+def oracle_rate_1thread(wl, budget_s: float = 3.0):
+    """Oracle samples/s on one host thread: centred 64x64 crops of successive
+    views until about budget_s of host time is spent."""
+    import oracle
+    vol, tf = wl["vol"], wl["tf"]
+    lo, hi = float(vol.min()), float(vol.max())
+    boxes = oracle.grid_partition(vol.shape[::-1], wl["grid"])
+    n = 0
+    k = 0
+    t = time.perf_counter()
+    while time.perf_counter() - t < budget_s and k < 64:
+        cam = wl["cams"][k % len(wl["cams"])]
+        W, H = cam["width"], cam["height"]
+        w, h = min(W, 64), min(H, 64)
+        n += oracle.render(vol, boxes, tf, lo, hi, cam, wl["step"], wl["ert"],
+                           crop=((W - w) // 2, (H - h) // 2, w, h), threads=1)["nsamples"]
+        k += 1
+    dt = time.perf_counter() - t
+    return dict(value=n / dt, unit=UNIT, cores=1, kind="oracle",
+                sample="%d centred 64x64 crops of successive views (%d samples, %.1f s, FP64, 1 thread)"
+                       % (k, n, dt))
+
+
 def oracle_rate(wl, budget_s: float = 12.0):
     """Oracle samples/s over whole frames of successive views, until about
     budget_s of host time is spent (every host core)."""
@@ -430,6 +453,7 @@ def run_ours(a):
         import oracle
         oracle.build()
         cpu, _, _ = oracle_rate(wl)
+        cpu["single_thread"] = oracle_rate_1thread(wl)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=K, warmup=a.warmup,
         ms_per_step=ms / K, higher_is_better=True, scaling="weak", vs_baseline=None,
