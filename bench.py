@@ -37,7 +37,7 @@ UNIT = "samples/s"
 # trilinear reconstruction 30, classification 19, accumulation 8, termination
 # test 1).
 FLOPS_PER_SAMPLE = 66
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128  # FP32 lanes per SM (sm_100 family)
 # kernel durations are taken from event pairs around the launches of every
 # KT_STRIDE-th timed frame (7 is coprime with the 8 orbit views)
 KT_STRIDE = 7
@@ -441,7 +441,8 @@ def run_ours(a):
     hbm_src = "of measured" if hbm else "of fallback"
     hbm = hbm or 6800.0
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    sms = torch.cuda.get_device_properties(local).multi_processor_count  # read from the device
+    fp32_peak = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
     march_tflops = FLOPS_PER_SAMPLE * per_frame_samples / (march_ms / 1e3) / 1e12
     mean_rect = sum(rect_px[vi] for vi in timed_views) / len(timed_views)
     comp_bytes = (mean_rect + W * H) * 16
@@ -470,8 +471,10 @@ def run_ours(a):
         roofline=dict(bound="alu", kernel="march", achieved=march_tflops, peak=fp32_peak, unit="TFLOP/s",
                       frac=march_tflops / fp32_peak,
                       traffic=recorded_traffic() if a.workload == "paper" else None,
-                      note="FP32 %d flops/sample x executed samples / mean march launch; peak = 152 SMs x "
-                           "128 lanes x 2 x %.0f MHz (derived)" % (FLOPS_PER_SAMPLE, sm_max)),
+                      sms=sms,
+                      note="FP32 %d flops/sample x executed samples / mean march launch; peak = %d SMs "
+                           "(cudaDeviceProp.multiProcessorCount) x 128 lanes x 2 x %.0f MHz (derived)"
+                           % (FLOPS_PER_SAMPLE, sms, sm_max)),
         roofline_l1=dict(note="ncu on the march: L1 data-pipe LSU wavefronts 74% of peak, issue slots "
                               "61%, top stall long scoreboard; L1 hit 78%, L2 hit 32% of the L1 misses, "
                               "DRAM traffic = compulsory quad bytes"),

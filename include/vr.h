@@ -276,6 +276,16 @@ vr_status vr_batch_autotune(vr_batch batch, void *stream, const char *cache_path
  * as many as fit); order 0 or 1 as for vr_batch_autotune. */
 vr_status vr_batch_configure(vr_batch batch, int packet_width, int blocks_per_sm, int order);
 vr_status vr_batch_release(vr_batch batch);
+/* Test hook for the bounded waits (the paper has no counterpart). Rebuilds the
+ * batch's graph so that each device-side wait gives up after `wait_limit`
+ * sleeps of about 128 ns (0 restores the default of 2^25, about 4 s) and the
+ * composite tiles of unit 0 wait for `extra_march` more finished march items
+ * than exist. With extra_march > 0 those waits cannot succeed: the first to give
+ * up sets the device error word, every other wait and claim stops, the launch
+ * ends with some renders incomplete, and the next vr_sync returns
+ * VR_ERR_TIMEOUT. Nothing faults or hangs. (0, 0) restores normal operation.
+ * VR_ERR_ARG for negative arguments. */
+vr_status vr_batch_debug_wait(vr_batch batch, int wait_limit, int extra_march);
 
 /* ---- differentiation ------------------------------------------------------ */
 
@@ -382,9 +392,10 @@ vr_status vr_debug_inject_fault(int kind, int after);
  * every GPU loading the library holds until the process exits. A frame whose
  * partial images (16 bytes per pixel of every brick's footprint rectangle)
  * would exceed it is rejected with VR_ERR_ARG before any device work.
- *   - Works on the current CUDA device. The first call on each device looks up
- *     the scratch address (cudaGetSymbolAddress); make that first call before
- *     any stream capture.
+ *   - Works on the current CUDA device. Every call looks up the scratch's
+ *     device address (cudaGetSymbolAddress) on that device, so the call stays
+ *     valid after a device reset; the first call on a device also loads the
+ *     library's device code there, so make it before any stream capture.
  *   - All calls on a device share the scratch: calls that overlap on the GPU
  *     (other streams, other threads) race; order them on one stream. Each call
  *     rewrites every scratch byte it reads, so nothing needs clearing.

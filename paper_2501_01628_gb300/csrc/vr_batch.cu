@@ -147,7 +147,10 @@ __global__ void __launch_bounds__(128, 9) batch_kernel(const __grid_constant__ B
             const int ntx = (V.W + kBatchCompW - 1) / kBatchCompW;
             const int cty = c / ntx, ctx = c - cty * ntx;
             const int tx0 = ctx * kBatchCompW, ty0 = cty * kBatchCompH;
-            if (tid == 0 && !wait_at_least(p.march_done + u, p.unit_march[u], p.wait_limit, p.error))
+            // (wait_extra raises unit 0's target past its item count: a test hook
+            // that makes this bounded wait give up; 0 in normal use)
+            if (tid == 0 && !wait_at_least(p.march_done + u, p.unit_march[u] + (u == 0 ? p.wait_extra : 0),
+                                           p.wait_limit, p.error))
                 atomicOr(p.error, 2);
             __syncthreads();
             const BrickLaunch *vb = p.vb + static_cast<long long>(w) * p.nb;
@@ -268,6 +271,8 @@ struct vr_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool counted = false;  // included in the context's live-object count
+    int dbg_wait_limit = 0;  // vr_batch_debug_wait: sleeps per wait (0 = default)
+    int dbg_wait_extra = 0;  // vr_batch_debug_wait: added to unit 0's composite target
 };
 
 namespace {
@@ -459,7 +464,8 @@ vr_status build(vr_batch b, int pw, int bps, int mode)
     p.march_done = b->d_march_done;
     p.comp_done = b->d_comp_done;
     p.error = ctx->d_error;
-    p.wait_limit = 1 << 25;  // about 4 s of 128 ns sleeps
+    p.wait_limit = b->dbg_wait_limit > 0 ? b->dbg_wait_limit : 1 << 25;  // default: about 4 s of 128 ns sleeps
+    p.wait_extra = b->dbg_wait_extra;
     // graph: reset the counters, then the single persistent launch
     VR_CUDA(ctx, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(b->d_claim, 0, sizeof(unsigned long long), b->cap);
@@ -645,6 +651,15 @@ vr_status vr_batch_configure(vr_batch b, int packet_width, int blocks_per_sm, in
         (order != 0 && order != 1))
         return fail(b->ctx, VR_ERR_ARG, "bad batch configuration");
     return build(b, packet_width, blocks_per_sm, order);
+}
+
+vr_status vr_batch_debug_wait(vr_batch b, int wait_limit, int extra_march)
+{
+    if (!b) return VR_ERR_ARG;
+    if (wait_limit < 0 || extra_march < 0) return fail(b->ctx, VR_ERR_ARG, "negative wait limit or extra count");
+    b->dbg_wait_limit = wait_limit;
+    b->dbg_wait_extra = extra_march;
+    return build(b, b->pw, b->bps, b->mode);
 }
 
 vr_status vr_batch_release(vr_batch b)

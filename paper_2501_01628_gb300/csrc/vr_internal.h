@@ -161,6 +161,7 @@ struct BatchParams {
     int *comp_done;                  // per unit: finished composite tiles
     int *error;                      // bit 1: a bounded wait gave up
     int wait_limit;                  // spin iterations (about 128 ns each) before giving up
+    int wait_extra;                  // added to unit 0's march target by composite waits (test hook; 0)
 };
 
 // Pack of all bricks of a volume in one launch: block j of brick b (counted

@@ -15,7 +15,6 @@
 // packing would need device memory.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "vr_internal.h"
@@ -29,24 +28,14 @@ constexpr size_t kScratchBytes = VR_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kTfBytes = 2 * 1024 * sizeof(float4);
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (looked up once per
-// device; the host-side symbol itself is not a device address).
-cudaError_t scratch_address(int device, void **out)
+// Device address of g_scratch on the current device. The host-side symbol is
+// not a device address; the lookup is repeated on every call (it is cheap once
+// the module is loaded), so a device reset or a re-created primary context
+// never leaves a stale address behind.
+cudaError_t scratch_address(void **out)
 {
-    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[device] = p;
-    }
-    *out = g_scratch_ptr[device];
-    return cudaSuccess;
+    *out = nullptr;
+    return cudaGetSymbolAddress(out, g_scratch);
 }
 
 __device__ __forceinline__ int find_brick_g(const MarchParams &p, int item)
@@ -286,10 +275,8 @@ extern "C" vr_status vr_render_frame_noalloc(const float *volume_dev, const int 
             pairs[8 * i + 4 + c] = b - a;
         }
 
-    int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess) return VR_ERR_CUDA;
     void *scratch = nullptr;
-    if (scratch_address(device, &scratch) != cudaSuccess) return VR_ERR_CUDA;
+    if (scratch_address(&scratch) != cudaSuccess || !scratch) return VR_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float4 *tf_dev = static_cast<float4 *>(scratch);
     float4 *partials = reinterpret_cast<float4 *>(static_cast<unsigned char *>(scratch) + kTfBytes);

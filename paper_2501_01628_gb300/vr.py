@@ -39,7 +39,7 @@ EXPORTS = (
     "vr_batch_autotune", "vr_batch_release", "vr_batch_configure", "vr_set_render_mode",
     "vr_set_opacity_correction", "vr_volume_update_async", "vr_set_packet_width",
     "vr_set_host_output_async", "vr_mesh_create", "vr_mesh_release", "vr_mesh_info",
-    "vr_render_mesh_frame", "vr_debug_inject_fault",
+    "vr_render_mesh_frame", "vr_debug_inject_fault", "vr_batch_debug_wait",
 )
 
 
@@ -99,6 +99,7 @@ _SIG = {
     "vr_batch_autotune": (_I, [_P, _P, ctypes.c_char_p, _P]),
     "vr_batch_release": (_I, [_P]),
     "vr_batch_configure": (_I, [_P, _I, _I, _I]),
+    "vr_batch_debug_wait": (_I, [_P, _I, _I]),
     "vr_set_render_mode": (_I, [_P, _I]),
     "vr_set_opacity_correction": (_I, [_P, ctypes.c_float]),
     "vr_set_packet_width": (_I, [_P, _I]),
@@ -152,18 +153,62 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _ptr_and_loc(x):
-    """(pointer, on_device, keepalive) of a contiguous float32 array/tensor."""
+# The C side receives bare pointers and cannot check a buffer's size or type,
+# so every array argument is checked here, before anything is launched: an
+# undersized or mistyped buffer would otherwise be read or written out of
+# bounds on the device. Image sizes come from the camera last set on a
+# context (recorded per handle), volume shapes from vr_volume_create.
+_cam_size = {}    # context handle -> (H, W)
+_tf_len = {}      # context handle -> entries of the transfer function
+_vol_shape = {}   # volume handle -> (Nz, Ny, Nx)
+_frame_size = {}  # frame handle -> (H, W)
+
+
+def _key(h):
+    return h.value if isinstance(h, ctypes.c_void_p) else int(h)
+
+
+def _array(x, what, shape=None, ndim=None, device=None, writable=False):
+    """(pointer, on_device, keepalive) of a float32 C-contiguous tensor/array
+    with the given shape (or number of dimensions); ValueError otherwise.
+    device: True = must be CUDA, False = must be host, None = either."""
     try:
         import torch
-        if isinstance(x, torch.Tensor):
-            if not x.is_contiguous():
-                raise ValueError("tensor must be contiguous")
-            return x.data_ptr(), int(x.is_cuda), x
+        is_t = isinstance(x, torch.Tensor)
     except ImportError:
-        pass
-    a = np.ascontiguousarray(x)
-    return a.ctypes.data, 0, a
+        is_t = False
+    if is_t:
+        dt_ok, contig, on_dev, shp = x.dtype == torch.float32, x.is_contiguous(), bool(x.is_cuda), tuple(x.shape)
+    elif isinstance(x, np.ndarray):
+        dt_ok, contig, on_dev, shp = x.dtype == np.float32, x.flags.c_contiguous, False, x.shape
+        if writable and not x.flags.writeable:
+            raise ValueError("%s must be writable" % what)
+    else:
+        raise ValueError("%s must be a torch tensor or numpy array" % what)
+    if not dt_ok:
+        raise ValueError("%s must be float32, got %s" % (what, x.dtype))
+    if ndim is not None and len(shp) != ndim:
+        raise ValueError("%s must have %d dimensions, got shape %s" % (what, ndim, shp))
+    if shape is not None and shp != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (what, tuple(shape), shp))
+    if not contig:
+        raise ValueError("%s must be contiguous" % what)
+    if device is True and not on_dev:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if device is False and on_dev:
+        raise ValueError("%s must be in host memory" % what)
+    if on_dev:
+        import torch
+        if x.device.index != torch.cuda.current_device():
+            raise ValueError("%s is on cuda:%d, not on the current device" % (what, x.device.index))
+    return (x.data_ptr() if is_t else x.ctypes.data), int(on_dev), x
+
+
+def _image_of(ctx, out, what="out"):
+    size = _cam_size.get(_key(ctx))
+    if size is None:
+        raise ValueError("no camera set on this context")
+    return _array(out, what, shape=size + (4,), writable=True)
 
 
 # --------------------------------------------------------------------------
@@ -179,6 +224,8 @@ def vr_create(cuda_device: int = 0):
 
 def vr_destroy(ctx):
     _check(lib().vr_destroy(ctx), ctx, "vr_destroy")
+    _cam_size.pop(_key(ctx), None)
+    _tf_len.pop(_key(ctx), None)
 
 
 def vr_sync(ctx, stream=None):
@@ -239,15 +286,14 @@ def vr_plan_view(dims, partition, cam: dict):
 def vr_volume_create(ctx, volume, storage: str = "f32", partition=None, stream=None):
     """volume: [Nz, Ny, Nx] float32 (numpy / torch, host or CUDA).
     partition: dict for make_partition (default: one brick)."""
-    ptr, on_dev, keep = _ptr_and_loc(volume)
-    if getattr(keep, "dtype", None) is not None and str(keep.dtype) not in ("float32", "torch.float32"):
-        raise TypeError("volume must be float32")
+    ptr, on_dev, keep = _array(volume, "volume", ndim=3)
     nz, ny, nx = tuple(keep.shape)
     dims = (ctypes.c_int * 3)(nx, ny, nz)
     part, pk = make_partition(**(partition or {}))
     h = ctypes.c_void_p()
     _check(lib().vr_volume_create(ctx, dims, DTYPES[storage], ctypes.byref(part), ptr, on_dev,
                                   _stream(stream), ctypes.byref(h)), ctx, "vr_volume_create")
+    _vol_shape[_key(h)] = (nz, ny, nx)
     return h
 
 
@@ -259,9 +305,10 @@ def vr_batch_create(ctx, vols, cams, out, vmins=None, vmaxs=None):
     cs = (vr_camera * len(cams))(*[camera_struct(c) for c in cams])
     lo = np.ascontiguousarray(vmins, dtype=np.float32) if vmins is not None else None
     hi = np.ascontiguousarray(vmaxs, dtype=np.float32) if vmaxs is not None else None
-    optr, oon, _ = _ptr_and_loc(out)
-    if not oon:
-        raise ValueError("out must be a CUDA tensor")
+    if (lo is not None and lo.size != nv) or (hi is not None and hi.size != nv):
+        raise ValueError("one vmin and one vmax per volume")
+    H, W = int(cams[0]["height"]), int(cams[0]["width"])
+    optr, oon, _ = _array(out, "out", shape=(nv * len(cams), H, W, 4), device=True)
     h = ctypes.c_void_p()
     _check(lib().vr_batch_create(ctx, nv, vh, lo.ctypes.data if lo is not None else None,
                                  hi.ctypes.data if hi is not None else None, len(cams), cs, optr,
@@ -286,39 +333,45 @@ def vr_batch_configure(batch, packet_width: int = 8, blocks_per_sm: int = 0, ord
            "vr_batch_configure")
 
 
+def vr_batch_debug_wait(batch, wait_limit: int = 0, extra_march: int = 0):
+    """Test hook: bounded waits give up after wait_limit sleeps (0: default), and
+    unit 0's composite waits for extra_march more march items than exist."""
+    _check(lib().vr_batch_debug_wait(batch, int(wait_limit), int(extra_march)), None, "vr_batch_debug_wait")
+
+
 def vr_batch_release(batch):
     _check(lib().vr_batch_release(batch), None, "vr_batch_release")
 
 
 def vr_volume_update(vol, volume, stream=None):
     """Re-pack `vol` from a float32 [Nz, Ny, Nx] array (same dims)."""
-    ptr, on_dev, keep = _ptr_and_loc(volume)
+    ptr, on_dev, keep = _array(volume, "volume", shape=_vol_shape.get(_key(vol)), ndim=3)
     _check(lib().vr_volume_update(vol, ptr, on_dev, _stream(stream)), None, "vr_volume_update")
 
 
 def vr_volume_update_async(vol, volume, stream=None):
     """Asynchronous re-pack on `stream` (host sources should be pinned)."""
-    ptr, on_dev, keep = _ptr_and_loc(volume)
+    ptr, on_dev, keep = _array(volume, "volume", shape=_vol_shape.get(_key(vol)), ndim=3)
     _check(lib().vr_volume_update_async(vol, ptr, on_dev, _stream(stream)), None, "vr_volume_update_async")
 
 
 def vr_render_backward(ctx, vol, grad_rgba, grad_tf, grad_density=None, stream=None):
     """Adds dL/d(table) to grad_tf and dL/d(voxels) to grad_density (CUDA float32
     tensors) for dL/dI = grad_rgba ([H, W, 4] CUDA float32)."""
-    g, gon, _ = _ptr_and_loc(grad_rgba)
-    t, ton, _ = _ptr_and_loc(grad_tf)
+    size = _cam_size.get(_key(ctx))
+    if size is None:
+        raise ValueError("no camera set on this context")
+    g, _, _ = _array(grad_rgba, "grad_rgba", shape=size + (4,), device=True)
+    t, _, _ = _array(grad_tf, "grad_tf", shape=(_tf_len.get(_key(ctx), -1), 4), device=True)
     d = None
     if grad_density is not None:
-        d, don, _ = _ptr_and_loc(grad_density)
-        if not don:
-            raise ValueError("grad_density must be a CUDA tensor")
-    if not (gon and ton):
-        raise ValueError("gradients must be CUDA tensors")
+        d, _, _ = _array(grad_density, "grad_density", shape=_vol_shape.get(_key(vol)), ndim=3, device=True)
     _check(lib().vr_render_backward(ctx, vol, g, t, d, _stream(stream)), ctx, "vr_render_backward")
 
 
 def vr_volume_release(vol):
     _check(lib().vr_volume_release(vol), None, "vr_volume_release")
+    _vol_shape.pop(_key(vol), None)
 
 
 def vr_volume_info(vol):
@@ -342,10 +395,15 @@ def vr_volume_read_brick(vol, brick: int, storage: str = "f32"):
 
 
 def vr_set_transfer_function(ctx, rgba, vmin: float, vmax: float):
-    ptr, on_dev, keep = _ptr_and_loc(rgba)
+    if isinstance(rgba, np.ndarray) or not hasattr(rgba, "data_ptr"):
+        rgba = np.ascontiguousarray(rgba, dtype=np.float32)
+    ptr, on_dev, keep = _array(rgba, "transfer function", ndim=2)
+    if keep.shape[1] != 4:
+        raise ValueError("transfer function must be (n, 4) RGBA")
     n = int(keep.shape[0])
     _check(lib().vr_set_transfer_function(ctx, ptr, n, float(vmin), float(vmax), on_dev), ctx,
            "vr_set_transfer_function")
+    _tf_len[_key(ctx)] = n
 
 
 def camera_struct(cam: dict) -> vr_camera:
@@ -364,6 +422,7 @@ def camera_struct(cam: dict) -> vr_camera:
 def vr_set_camera(ctx, cam: dict):
     c = camera_struct(cam)
     _check(lib().vr_set_camera(ctx, ctypes.byref(c)), ctx, "vr_set_camera")
+    _cam_size[_key(ctx)] = (c.height, c.width)
 
 
 def vr_set_render_params(ctx, step_voxels: float = 0.5, ert_alpha: float = 1.0):
@@ -434,6 +493,7 @@ def vr_render_partials(ctx, vol, stream=None):
     h = ctypes.c_void_p()
     _check(lib().vr_render_partials(ctx, vol, ctypes.byref(h), _stream(stream)), ctx,
            "vr_render_partials")
+    _frame_size[_key(h)] = _cam_size[_key(ctx)]
     return h
 
 
@@ -455,16 +515,20 @@ def vr_frame_partial(frame, brick: int):
 
 
 def vr_composite(ctx, frame, out, stream=None):
-    ptr, on_dev, _ = _ptr_and_loc(out)
+    size = _frame_size.get(_key(frame))
+    if size is None:
+        raise ValueError("unknown frame")
+    ptr, on_dev, _ = _array(out, "out", shape=size + (4,), writable=True)
     _check(lib().vr_composite(ctx, frame, ptr, on_dev, _stream(stream)), ctx, "vr_composite")
 
 
 def vr_frame_release(frame):
     _check(lib().vr_frame_release(frame), None, "vr_frame_release")
+    _frame_size.pop(_key(frame), None)
 
 
 def vr_render_frame(ctx, vol, out, stream=None):
-    ptr, on_dev, _ = _ptr_and_loc(out)
+    ptr, on_dev, _ = _image_of(ctx, out)
     _check(lib().vr_render_frame(ctx, vol, ptr, on_dev, _stream(stream)), ctx, "vr_render_frame")
 
 
@@ -500,7 +564,7 @@ def vr_mesh_info(mesh):
 
 
 def vr_render_mesh_frame(ctx, mesh, out, stream=None):
-    ptr, on_dev, _ = _ptr_and_loc(out)
+    ptr, on_dev, _ = _image_of(ctx, out)
     _check(lib().vr_render_mesh_frame(ctx, mesh, ptr, on_dev, _stream(stream)), ctx, "vr_render_mesh_frame")
 
 
@@ -509,8 +573,8 @@ def vr_render_frame_noalloc(volume, partition, tf, vmin: float, vmax: float, cam
     """Frame without device allocation: `volume` and `out` are caller-owned CUDA
     tensors ([Nz, Ny, Nx] and [H, W, 4] float32); scratch is the library's static
     device array (see include/vr.h)."""
-    vptr, von, vk = _ptr_and_loc(volume)
-    optr, oon, _ = _ptr_and_loc(out)
+    vptr, von, vk = _array(volume, "volume", ndim=3)
+    optr, oon, _ = _array(out, "out", shape=(int(cam["height"]), int(cam["width"]), 4), writable=True)
     if not (von and oon):
         raise ValueError("volume and out must be CUDA tensors")
     nz, ny, nx = tuple(vk.shape)

@@ -133,3 +133,62 @@ def test_batching_workload_sampled(vr):
         for v in vols:
             vr.vr_volume_release(v)
         vr.vr_destroy(ctx)
+
+
+def test_bounded_wait_gives_up_and_reports_timeout(vr):
+    """The batched kernel's waits are bounded. A test hook raises unit 0's
+    composite target past its march item count, so those waits can never
+    succeed, and shortens every wait to 64 sleeps: the launch must end within
+    milliseconds, vr_sync must return VR_ERR_TIMEOUT, and the next launch with
+    the hook cleared must be bit-identical to plain renders. Nothing faults:
+    the wait gives up, sets the error word, and every other claim stops."""
+    import time
+    import torch
+    n = 32
+    draws = synth.draw_fields(seed=41, n_fields=1)
+    rng = np.random.default_rng(41)
+    tf = synth.random_tf(rng, alpha_max=0.12)
+    part = dict(kind="grid", grid=(2, 2, 1))
+    cams = [synth.orbit_camera(48, 40, az) for az in (20.0, 150.0, 260.0)]
+    ctx = vr.vr_create(0)
+    vols, ranges = [], []
+    try:
+        for s in range(2):
+            src = synth.field_volume_torch(draws[0], s, n)
+            ranges.append((float(src.min()), float(src.max())))
+            vols.append(vr.vr_volume_create(ctx, src, "f32", part))
+        vr.vr_set_transfer_function(ctx, tf, 0.0, 1.0)
+        vr.vr_set_render_params(ctx, 0.5, 1.0)
+        nr = len(vols) * len(cams)
+        out = torch.full((nr, 40, 48, 4), float("nan"), device="cuda")
+        b = vr.vr_batch_create(ctx, vols, cams, out, vmins=[r[0] for r in ranges],
+                               vmaxs=[r[1] for r in ranges])
+        refs = [_plain(vr, ctx, vol, cam, lo, hi, tf).clone()
+                for vol, (lo, hi) in zip(vols, ranges) for cam in cams]
+        vr.vr_sync(ctx)
+        for order in (0, 1):  # render-major and brick-major units
+            vr.vr_batch_configure(b, 8, 0, order)
+            vr.vr_batch_debug_wait(b, 64, 1)
+            out.fill_(float("nan"))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            vr.vr_batch_launch(b)
+            with pytest.raises(vr.VrError) as e:
+                vr.vr_sync(ctx)
+            elapsed = time.perf_counter() - t0
+            assert e.value.status == vr.VR_ERR_TIMEOUT
+            assert elapsed < 0.5, elapsed  # the 2^25-sleep default would take seconds
+            vr.vr_sync(ctx)  # the error word was cleared by the report
+            vr.vr_batch_debug_wait(b, 0, 0)
+            out.fill_(float("nan"))
+            vr.vr_batch_launch(b)
+            vr.vr_sync(ctx)
+            for r, ref in enumerate(refs):
+                assert torch.equal(out[r], ref), (order, r)
+        with pytest.raises(vr.VrError):
+            vr.vr_batch_debug_wait(b, -1, 0)
+        vr.vr_batch_release(b)
+    finally:
+        for v in vols:
+            vr.vr_volume_release(v)
+        vr.vr_destroy(ctx)

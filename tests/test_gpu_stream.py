@@ -1,10 +1,12 @@
 """Time-step streaming through a fixed device budget: the renders of each time
 step equal those of a volume created directly from that step, whether or not
-the next step's upload overlaps them."""
+the next step's upload overlaps them, and match the FP64 oracle on that step's
+values (Sec. 4: time steps are loaded and later evicted)."""
 import numpy as np
 import pytest
 
 from paper_2501_01628_gb300 import synth
+from gpu_helpers import compare_envelope, oracle_env
 
 pytestmark = pytest.mark.gpu
 
@@ -49,5 +51,11 @@ def test_streamed_steps_equal_direct_renders(vr, slots, prefetch):
                 assert torch.equal(g, ref), t
             vr.vr_volume_release(v)
         vr.vr_sync(ctx)
+        # against the oracle: every step at one view, and every view at the last step
+        boxes = vr.vr_partition_boxes((n,) * 3, part)
+        checks = [(t, 1) for t in range(steps)] + [(steps - 1, 0), (steps - 1, 2)]
+        for t, c in checks:
+            env = oracle_env(host[t].numpy(), boxes, tf, 0.0, 1.1, cams[c])
+            compare_envelope(got[t][c].cpu().numpy().astype(np.float64), env)
     finally:
         vr.vr_destroy(ctx)

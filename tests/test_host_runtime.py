@@ -124,3 +124,47 @@ def test_visibility_order_and_footprints_against_oracle(vr, case):
             mask = np.ones((H, W), bool)
             mask[y0:y0 + h, x0:x0 + w] = False
             assert np.all(ref["partials"][b][mask] == 0), (b, (x0, y0, w, h))
+
+
+def test_binding_rejects_mistyped_or_misshaped_buffers_before_any_launch():
+    """The C side gets bare pointers and cannot check sizes, so the binding
+    refuses a wrong dtype, rank, shape, layout or memory space up front (a
+    16-bit volume read as float32, or an image smaller than H x W x 4, would be
+    an out-of-bounds access on the device). Nothing here reaches the library."""
+    import ctypes
+    import torch
+    from paper_2501_01628_gb300 import vr
+    cam = synth.orbit_camera(8, 6, 30.0)
+    part = dict(kind="grid", grid=(1, 1, 1))
+    tf = synth.constant_tf([1, 1, 1, 0.1])
+    good_vol = torch.zeros((4, 4, 4))
+    good_out = torch.zeros((6, 8, 4))
+    bad = [
+        (torch.zeros((4, 4, 4), dtype=torch.bfloat16), good_out, "float32"),
+        (torch.zeros((4, 16)), good_out, "3 dimensions"),
+        (torch.zeros((4, 4, 8))[:, :, ::2], good_out, "contiguous"),
+        (good_vol, torch.zeros((8, 6, 4)), "shape"),
+        (good_vol, torch.zeros((6, 8, 4), dtype=torch.float64), "float32"),
+        (good_vol, good_out, "CUDA"),  # host memory where device memory is required
+    ]
+    for vol, out, msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            vr.vr_render_frame_noalloc(vol, part, tf, 0.0, 1.0, cam, out)
+    # context calls: the image must match the camera last set on the context
+    fake = ctypes.c_void_p(0x1234)
+    with pytest.raises(ValueError, match="no camera"):
+        vr.vr_render_frame(fake, None, good_out)
+    vr._cam_size[vr._key(fake)] = (6, 8)
+    try:
+        for out, msg in ((torch.zeros((6, 8, 3)), "shape"), (torch.zeros(6 * 8 * 4), "shape"),
+                         (torch.zeros((6, 8, 4), dtype=torch.float16), "float32"),
+                         (np.zeros((6, 8, 4), np.float64), "float32"),
+                         (np.zeros((8, 6, 4), np.float32).transpose(1, 0, 2), "contiguous")):
+            with pytest.raises(ValueError, match=msg):
+                vr.vr_render_frame(fake, None, out)
+        with pytest.raises(ValueError, match="float32"):
+            vr.vr_volume_create(fake, np.zeros((4, 4, 4), np.float64))
+        with pytest.raises(ValueError, match="CUDA"):
+            vr.vr_render_backward(fake, None, good_out, torch.zeros((2, 4)))
+    finally:
+        vr._cam_size.pop(vr._key(fake), None)

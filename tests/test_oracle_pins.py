@@ -446,3 +446,101 @@ def test_opacity_correction_at_the_reference_step_is_the_identity():
     a = oracle.render(vol, boxes, tf, lo, hi, cam, 0.5)
     b = oracle.render(vol, boxes, tf, lo, hi, cam, 0.5, opacity_ref_step=0.5)
     np.testing.assert_array_equal(a["img"], b["img"])
+
+
+# --------------------------------------------------------------------------
+# 16-bit storage decoders: every code against its IEEE-754 definition
+# --------------------------------------------------------------------------
+
+
+def _decode_all_codes(codes, dtype):
+    """Oracle value of each 16-bit code: the codes form a 256 x 256 x 1 volume
+    and each is sampled at its own voxel centre, where the trilinear weights
+    are exactly (1, 0, ..., 0) (every neighbour must then be finite)."""
+    vol = np.ascontiguousarray(codes.reshape(1, 256, 256))
+    j, i = np.divmod(np.arange(codes.size), 256)
+    pts = np.stack([(i + 0.5) / 256, (j + 0.5) / 256, np.full(i.size, 0.5 / 256)], axis=1)
+    return oracle.sample(vol, pts, dtype=dtype)
+
+
+def _uniform_code_value(code, dtype):
+    """Oracle value inside a 2x2x2 volume whose voxels all hold one code,
+    sampled at the volume centre (all eight weights 1/8)."""
+    vol = np.full((2, 2, 2), code, dtype=np.uint16)
+    return oracle.sample(vol, [[0.5, 0.5, 0.5]], dtype=dtype)[0]
+
+
+def test_f16_decoder_every_code():
+    # IEEE binary16: numpy's float16 is the independent definition; this covers
+    # the subnormals (exponent field 0: m * 2^-24), the normals, and +-0
+    codes = np.arange(65536, dtype=np.uint32).astype(np.uint16)
+    want = codes.view(np.float16).astype(np.float64)
+    finite = np.isfinite(want)
+    got = _decode_all_codes(np.where(finite, codes, 0).astype(np.uint16), oracle.F16)
+    np.testing.assert_array_equal(got[finite], want[finite])
+    # a few values written out by hand from the format's definition
+    assert got[0x0001] == 2.0 ** -24 and got[0x03FF] == 1023 * 2.0 ** -24
+    assert got[0x0400] == 2.0 ** -14 and got[0x3C00] == 1.0 and got[0x7BFF] == 65504.0
+    assert got[0xC000] == -2.0 and got[0x8001] == -(2.0 ** -24)
+    # exponent field 31: infinities and NaNs
+    assert _uniform_code_value(0x7C00, oracle.F16) == math.inf
+    assert _uniform_code_value(0xFC00, oracle.F16) == -math.inf
+    for c in (0x7C01, 0x7E00, 0xFFFF):
+        assert math.isnan(_uniform_code_value(c, oracle.F16))
+
+
+def test_bf16_decoder_every_code():
+    # bfloat16 is the top half of an IEEE binary32: the value of code c is the
+    # float32 whose bit pattern is c << 16
+    codes = np.arange(65536, dtype=np.uint32)
+    with np.errstate(invalid="ignore"):
+        want = (codes << 16).view(np.float32).astype(np.float64)
+    finite = np.isfinite(want)
+    got = _decode_all_codes(np.where(finite, codes, 0).astype(np.uint16), oracle.BF16)
+    np.testing.assert_array_equal(got[finite], want[finite])
+    assert got[0x3F80] == 1.0 and got[0xC000] == -2.0 and got[0x0001] == 2.0 ** -133
+    assert got[0x0080] == 2.0 ** -126 and got[0x7F7F] == (2 - 2.0 ** -7) * 2.0 ** 127
+    assert _uniform_code_value(0x7F80, oracle.BF16) == math.inf
+    assert _uniform_code_value(0xFF80, oracle.BF16) == -math.inf
+    for c in (0x7F81, 0x7FC0, 0xFFFF):
+        assert math.isnan(_uniform_code_value(c, oracle.BF16))
+
+
+# --------------------------------------------------------------------------
+# Perspective geometry on non-square images: square pixels on the image plane
+# --------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("W,H", [(16, 9), (9, 16), (37, 5)])
+def test_perspective_pixels_are_square_on_non_square_images(W, H):
+    """A pinhole camera with vertical field of view fovy puts pixel centres on
+    a regular grid of SQUARE cells on the image plane at unit distance: the
+    rows span 2 tan(fovy/2) in H steps, and the columns use the same spacing,
+    so the horizontal extent is the aspect ratio W/H times the vertical one.
+    Checked on the rays' intersections with that plane, in the camera basis
+    built here from the camera's definition (f = dir, r = up x f, u = f x r)."""
+    fovy = 50.0
+    cam = synth.orbit_camera(W, H, 115.0, radius=1.7, elevation_deg=15.0, fovy_deg=fovy)
+    f = np.asarray(cam["dir"], float)
+    f /= np.linalg.norm(f)
+    r = np.cross(np.asarray(cam["up"], float), f)
+    r /= np.linalg.norm(r)
+    u = np.cross(f, r)
+    x = np.zeros((H, W))
+    y = np.zeros((H, W))
+    for py in range(H):
+        for px in range(W):
+            o, d = oracle.primary_ray(cam, px, py)
+            np.testing.assert_allclose(o, cam["eye"], atol=1e-15)
+            hit = d / np.dot(d, f)  # intersection with the plane at unit distance
+            x[py, px], y[py, px] = np.dot(hit, r), np.dot(hit, u)
+    step = 2 * math.tan(math.radians(fovy / 2)) / H
+    np.testing.assert_allclose(np.diff(y, axis=0), step, rtol=1e-12)  # rows: fovy over H
+    np.testing.assert_allclose(np.diff(x, axis=1), step, rtol=1e-12)  # columns: same pitch
+    np.testing.assert_allclose(np.diff(y, axis=1), 0, atol=1e-13)
+    np.testing.assert_allclose(np.diff(x, axis=0), 0, atol=1e-13)
+    # centred on the view direction; half-pixel inset at the edges
+    np.testing.assert_allclose(x[:, 0] + x[:, -1], 0, atol=1e-13)
+    np.testing.assert_allclose(y[0] + y[-1], 0, atol=1e-13)
+    np.testing.assert_allclose(x[0, -1], (W / 2 - 0.5) * step, rtol=1e-12)
+    np.testing.assert_allclose(y[-1, 0], (H / 2 - 0.5) * step, rtol=1e-12)
