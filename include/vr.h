@@ -387,10 +387,11 @@ vr_status vr_debug_inject_fault(int kind, int after);
  * dims[0] x dims[1] x dims[2] voxels, read in place (no packed bricks); the
  * image goes to `out_rgba_dev` (H x W x 4 float32, device). `tf_rgba` (n_tf
  * RGBA entries, 2 <= n_tf <= 1024) and `cam` are host memory. Nothing is
- * allocated on the device: the per-brick partial images and the transfer
- * function live in one static device array of VR_NOALLOC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits. A frame whose
- * partial images (16 bytes per pixel of every brick's footprint rectangle)
+ * allocated on the device: the per-brick partial images, the composite's tile
+ * masks and the transfer function live in one static device array of
+ * VR_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits. A frame whose partial images (16 bytes per pixel of every
+ * brick's footprint rectangle) and tile masks (16 bytes per 32 x 16 pixels)
  * would exceed it is rejected with VR_ERR_ARG before any device work.
  *   - Works on the current CUDA device. Every call looks up the scratch's
  *     device address (cudaGetSymbolAddress) on that device, so the call stays

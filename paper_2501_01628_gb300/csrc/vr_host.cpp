@@ -418,6 +418,10 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
         items += L.tiles_x * tiles_y;
     }
     fr.total_px = px;
+    fr.tiles_x = (c.width + kCompW - 1) / kCompW;
+    fr.tiles_y = (c.height + kCompTileH - 1) / kCompTileH;
+    fr.pool_px = px + static_cast<long long>(fr.tiles_x) * fr.tiles_y;
+    fr.masks_ready = false;
     for (int a = 0; a < 3; ++a) {
         mp.eye[a] = static_cast<float>(c.eye[a]);
         mp.r[a] = static_cast<float>(B.r[a]);
@@ -492,12 +496,18 @@ vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s)
     static thread_local MarchParams mp;  // ~12 KB: keep off the stack
     vr_status st = prepare_frame(ctx, vol, fr, mp);
     if (st != VR_OK) return st;
-    st = ensure_frame(ctx, fr, std::max(fr.total_px, 1LL));
+    st = ensure_frame(ctx, fr, std::max(fr.pool_px, 1LL));
     if (st != VR_OK) return st;
     mp.partials = fr.d_part;
+    // the march grid's first blocks write the composite's tile masks
+    mp.tile_mask = reinterpret_cast<uint4 *>(fr.d_part + fr.total_px);
+    mp.mask_tiles_x = fr.tiles_x;
+    mp.mask_tiles_y = fr.tiles_y;
+    mp.mask_blocks = (fr.tiles_x * fr.tiles_y + kMaskThreads - 1) / kMaskThreads;
     const int t = timing_begin(ctx, 0, s);
     VR_LAUNCH(ctx, launch_march(mp, vol->dtype, s));
     timing_end(ctx, t, s);
+    fr.masks_ready = true;
     return VR_OK;
 }
 
@@ -515,24 +525,23 @@ vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s)
     if (nf > 0 && !radix)
         return fail(ctx, VR_ERR_ARG, "composite schedule factors do not multiply to the brick count");
     cp.n_levels = radix ? nf : 1;
-    for (int j = 0; j < fr.nb; ++j) {
-        cp.order[j] = fr.order[j];
-        int c = 0;
-        if (radix) {
-            long long m = j + 1;
-            while (c < nf - 1 && m % ctx->factors[c] == 0) {
-                m /= ctx->factors[c];
-                ++c;
-            }
-        }
-        cp.carry[j] = static_cast<unsigned char>(c);
-    }
+    // group[l]: partials per level-l group of the association tree
+    cp.group[0] = 1;
+    for (int l = 1; l < cp.n_levels; ++l) cp.group[l] = cp.group[l - 1] * ctx->factors[l - 1];
+    for (int j = 0; j < fr.nb; ++j) cp.order[j] = fr.order[j];
     for (int b = 0; b < fr.nb; ++b) {
         std::memcpy(cp.rect[b], &fr.rects[4 * b], 4 * sizeof(int));
         cp.poff[b] = fr.poff[b];
     }
     cp.partials = fr.d_part;
     cp.out = out;
+    cp.tile_mask = reinterpret_cast<uint4 *>(fr.d_part + fr.total_px);
+    cp.tiles_x = fr.tiles_x;
+    cp.tiles_y = fr.tiles_y;
+    if (!fr.masks_ready) {  // a march that does not write them (meshes)
+        VR_LAUNCH(ctx, launch_tile_masks(cp, s));
+        fr.masks_ready = true;
+    }
     const int t = timing_begin(ctx, 1, s);
     VR_LAUNCH(ctx, launch_composite(cp, s));
     timing_end(ctx, t, s);
@@ -918,7 +927,7 @@ vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_d
     // forward partials (recomputed: nothing per sample is kept from the forward call)
     vr_status st = prepare_frame(ctx, vol, fr, mp);
     if (st != VR_OK) return st;
-    st = ensure_frame(ctx, fr, std::max(fr.total_px, 1LL));
+    st = ensure_frame(ctx, fr, std::max(fr.pool_px, 1LL));
     if (st != VR_OK) return st;
     mp.partials = fr.d_part;
     mp.sample_counter = nullptr;

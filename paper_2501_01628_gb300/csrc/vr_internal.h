@@ -23,6 +23,8 @@ constexpr int kTileH = 8;
 constexpr int kCompW = 32;
 constexpr int kCompH = 8;
 constexpr int kCompRows = 2;
+constexpr int kCompTileH = kCompH * kCompRows;  // forward composite tile: kCompW x kCompTileH pixels
+constexpr int kMaskThreads = 128;                // threads (tiles) per block of the tile-mask pass
 
 // Brick storage index of quad (i, j, k): quads are grouped in 2x2x2 blocks of
 // 128 bytes (one L1 line for float32), blocks x-fastest; nbx, nby = blocks per
@@ -72,8 +74,13 @@ struct MarchParams {
     unsigned long long *sample_counter;  // non-null: count executed samples
     int *count_error;   // device error word; bit 4: in a counting launch, an executed
                         // sample's quad index fell outside its brick's storage
+    // composite tile masks written by the first mask_blocks blocks of the
+    // march grid (null: none): bit j of tile t's mask = the brick at visibility
+    // position j overlaps composite tile t (kCompW x kCompTileH pixels)
+    uint4 *tile_mask;
+    int mask_tiles_x, mask_tiles_y, mask_blocks;
     int nb;
-    int n_items;
+    int n_items;        // march work items (the grid adds mask_blocks in front)
     int order[kMaxBricks];  // brick ids front to back (ray-state cycling)
     BrickLaunch b[kMaxBricks];
 };
@@ -83,11 +90,13 @@ struct CompositeParams {
     int nb;
     int n_levels;                     // 1 = direct
     int order[kMaxBricks];            // brick ids front to back
-    unsigned char carry[kMaxBricks];  // levels to carry after position j
+    int group[kMaxFactors];           // radix-k: group[l] = f_0 f_1 ... f_{l-1} partials per level-l group
     int rect[kMaxBricks][4];          // by brick id
     long long poff[kMaxBricks];       // by brick id
     const float4 *partials;
     float4 *out;
+    uint4 *tile_mask;                 // per tile: visibility positions of the bricks overlapping it
+    int tiles_x, tiles_y;             // composite tiles per row / column (kCompW x kCompTileH)
 };
 
 // Composite adjoint: the composite's layout plus the image gradient and the
@@ -189,6 +198,8 @@ cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s);
 cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s);
 cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out, cudaStream_t s);
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s);
+// Tile masks of p (p.tile_mask) for frames whose march did not write them.
+cudaError_t launch_tile_masks(const CompositeParams &p, cudaStream_t s);
 cudaError_t launch_composite_grad(const CompositeGradParams &p, cudaStream_t s);
 cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, vr_dtype dtype, cudaStream_t s);
 // Persistent batched kernel: cooperative launch of `blocks` blocks of 128 threads.

@@ -61,6 +61,42 @@ __global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ PackP
 }
 
 // ---------------------------------------------------------------------------
+// Composite tile masks: one thread per composite tile (kCompW x kCompTileH
+// pixels) sets bit j of its 128-bit mask when the brick at visibility position
+// j has a non-empty footprint rectangle that overlaps the tile. Every thread
+// walks the positions in the same order, so the rectangle reads are uniform
+// across the warp (broadcast, not per-lane gathers).
+// ---------------------------------------------------------------------------
+template <typename RectOf>
+__device__ __forceinline__ void write_tile_mask(int tile, int tiles_x, int tiles_y, int nb, const int *order,
+                                                RectOf rect_of, uint4 *mask)
+{
+    if (tile >= tiles_x * tiles_y) return;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int x0 = tx * kCompW, y0 = ty * kCompTileH;
+    unsigned long long lo = 0, hi = 0;
+    for (int j = 0; j < nb; ++j) {
+        const int4 r = rect_of(order[j]);
+        const bool ov = r.z > 0 && r.w > 0 && r.x < x0 + kCompW && x0 < r.x + r.z && r.y < y0 + kCompTileH &&
+                        y0 < r.y + r.w;
+        if (ov) {
+            if (j < 64) lo |= 1ull << j;
+            else hi |= 1ull << (j - 64);
+        }
+    }
+    mask[tile] = make_uint4(static_cast<unsigned>(lo), static_cast<unsigned>(lo >> 32), static_cast<unsigned>(hi),
+                            static_cast<unsigned>(hi >> 32));
+}
+
+// Stand-alone mask pass, for frames whose march does not write the masks.
+__global__ void __launch_bounds__(kMaskThreads) tile_mask_kernel(const __grid_constant__ CompositeParams p)
+{
+    write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.tiles_x, p.tiles_y, p.nb, p.order,
+                    [&](int b) { return make_int4(p.rect[b][0], p.rect[b][1], p.rect[b][2], p.rect[b][3]); },
+                    p.tile_mask);
+}
+
+// ---------------------------------------------------------------------------
 // March: one thread per pixel of a brick's footprint. A block is a tile of
 // 2x2 warp packets of pw x (32/pw) pixels (pw = p.pw: 4, 8 or 16). The transfer
 // function is read as (T[i], T[i+1]-T[i]) pairs (the last difference is 0)
@@ -69,11 +105,18 @@ __global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ PackP
 template <typename S, bool COUNT, bool OPC>
 __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ MarchParams p)
 {
-    // the composite launched after this march may start (and compact its tile
-    // lists) once every block of this grid is running; it reads the partials
-    // only after this grid has completed
+    // the composite launched after this march may start once every block of
+    // this grid is running; it reads the masks and partials only after this
+    // grid has completed
     asm volatile("griddepcontrol.launch_dependents;");
-    const int item = blockIdx.x;
+    if (static_cast<int>(blockIdx.x) < p.mask_blocks) {  // the composite's tile masks
+        write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.mask_tiles_x, p.mask_tiles_y, p.nb, p.order,
+                        [&](int b) { return make_int4(p.b[b].rect[0], p.b[b].rect[1], p.b[b].rect[2],
+                                                      p.b[b].rect[3]); },
+                        p.tile_mask);
+        return;
+    }
+    const int item = blockIdx.x - p.mask_blocks;
     const int bi = find_brick(p, item);
     const BrickLaunch &B = p.b[bi];
     const int local = item - B.item_begin;
@@ -126,105 +169,119 @@ __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Composite: one 32x8-thread block per 32x16 image tile, one thread per pixel
-// of each of the tile's two 32x8 halves; partials are combined front to back
-// with "over" along the configured association tree.
+// Composite: one 32x8-thread block per kCompW x kCompTileH image tile, one
+// thread per pixel of each of the tile's kCompRows 32x8 slabs; partials are
+// combined front to back with "over" along the configured association tree.
 // ---------------------------------------------------------------------------
-// Per tile, warp 0 first compacts the bricks whose rectangles overlap the tile,
-// in visibility order. Absent partials are the identity of "over", so only the
-// association tree's carries at skipped positions matter; consecutive carries
-// compose to the deepest one, so each listed brick carries max(carry) up to the
-// next listed position.
+// The tile's mask (one 16-byte load, the same for the whole block) lists the
+// visibility positions of the bricks that overlap it. Absent partials are the
+// identity of "over", so only the association tree's carries at skipped
+// positions matter, and consecutive carries compose to the deepest one: before
+// the brick at position j, after the previous listed position i, the levels
+// completed anywhere in [i, j) are merged. Level l (>= 1) completes after
+// position q when (q + 1) is a multiple of group[l], so the deepest level
+// completed in [i, j) is the largest l with j / group[l] != i / group[l].
+// Partial loads for up to kBatch listed bricks and all kCompRows pixels are
+// issued before any is combined.
+template <int LEVELS>
+__device__ __forceinline__ int carried_levels(const CompositeParams &p, int i, int j)
+{
+    int c = 0;
+#pragma unroll
+    for (int l = 1; l < LEVELS; ++l)
+        if (l < p.n_levels && j / p.group[l] != i / p.group[l]) c = l;
+    return c;
+}
+
 template <int LEVELS>
 __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ CompositeParams p)
 {
-    __shared__ int s_brick[kMaxBricks];
-    __shared__ int s_pos[kMaxBricks + 1];
-    __shared__ unsigned char s_carry[kMaxBricks];
-    __shared__ int s_m;
-    const int tx0 = blockIdx.x * kCompW, ty0 = blockIdx.y * (kCompH * kCompRows);
-    const int tid = threadIdx.y * kCompW + threadIdx.x;
-    if (tid < 32) {
-        int m = 0;
-        for (int j0 = 0; j0 < p.nb; j0 += 32) {
-            const int j = j0 + tid;
-            bool ov = false;
-            int b = 0;
-            if (j < p.nb) {
-                b = p.order[j];
-                const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
-                ov = x0 < tx0 + kCompW && tx0 < x0 + w && y0 < ty0 + kCompH * kCompRows && ty0 < y0 + h;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, ov);
-            if (ov) {
-                const int at = m + __popc(bal & ((1u << tid) - 1u));
-                s_brick[at] = b;
-                s_pos[at] = j;
-            }
-            m += __popc(bal);
-        }
-        __syncwarp();
-        if (tid == 0) {
-            s_m = m;
-            s_pos[m] = p.nb;
-        }
-        __syncwarp();
-        if (LEVELS > 1)
-            for (int i = tid; i < m; i += 32) {
-                int c = 0;
-                for (int j = s_pos[i]; j < s_pos[i + 1]; ++j) c = max(c, static_cast<int>(p.carry[j]));
-                s_carry[i] = static_cast<unsigned char>(c);
-            }
-    }
-    __syncthreads();
-    // launched as a programmatic dependent of the march: wait here for the
-    // preceding grid's completion and memory (the tile list above reads only
-    // kernel parameters)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int m = s_m;
+    constexpr int kBatch = 4;
+    const int tx0 = blockIdx.x * kCompW, ty0 = blockIdx.y * kCompTileH;
     const int px = tx0 + threadIdx.x;
-    for (int half = 0; half < kCompRows; ++half) {
-        const int py = ty0 + threadIdx.y + kCompH * half;
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 acc[LEVELS];
+    // launched as a programmatic dependent of the march: wait for the preceding
+    // grid's completion and memory (the masks and partials are its output)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const uint4 mk = __ldg(p.tile_mask + blockIdx.y * p.tiles_x + blockIdx.x);
+    // positions not yet combined: 0-63 in rest0, 64-127 in rest1
+    unsigned long long rest0 = static_cast<unsigned long long>(mk.x) | (static_cast<unsigned long long>(mk.y) << 32);
+    unsigned long long rest1 = static_cast<unsigned long long>(mk.z) | (static_cast<unsigned long long>(mk.w) << 32);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acc[kCompRows][LEVELS];
 #pragma unroll
-        for (int l = 0; l < LEVELS; ++l) acc[l] = zero;
-        constexpr int kBatch = 4;  // partial loads in flight before they are combined
-        for (int i0 = 0; i0 < m; i0 += kBatch) {
-            float4 v[kBatch];
+    for (int r = 0; r < kCompRows; ++r)
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                v[u] = zero;
-                if (i0 + u < m) {
-                    const int b = s_brick[i0 + u];
-                    const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
-                    if (px >= x0 && px < x0 + w && py >= y0 && py < y0 + h)
-                        v[u] = __ldcs(p.partials + p.poff[b] + static_cast<long long>(py - y0) * w + (px - x0));
-                }
+        for (int l = 0; l < LEVELS; ++l) acc[r][l] = zero;
+    // merge the c lowest levels upwards, acc[r][l + 1] <- acc[r][l + 1] over acc[r][l]
+    auto carry = [&](int c) {
+#pragma unroll
+        for (int r = 0; r < kCompRows; ++r)
+#pragma unroll
+            for (int l = 0; l + 1 < LEVELS; ++l) {
+                const bool m = l < c;
+                const float4 merged = over(acc[r][l + 1], acc[r][l]);
+                acc[r][l + 1] = m ? merged : acc[r][l + 1];
+                acc[r][l] = m ? zero : acc[r][l];
             }
+    };
+    int prev = -1;  // visibility position of the last brick combined
+    for (;;) {
+        int pos[kBatch];
+        int cnt = 0;
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                if (i0 + u < m) {
-                    acc[0] = over(acc[0], v[u]);
-                    if (LEVELS > 1) {
-                        const int c = s_carry[i0 + u];
+        for (int u = 0; u < kBatch; ++u) {
+            pos[u] = -1;
+            if (rest0) {
+                pos[u] = __ffsll(static_cast<long long>(rest0)) - 1;
+                rest0 &= rest0 - 1;
+                ++cnt;
+            } else if (rest1) {
+                pos[u] = 63 + __ffsll(static_cast<long long>(rest1));
+                rest1 &= rest1 - 1;
+                ++cnt;
+            }
+        }
+        if (cnt == 0) break;
+        float4 v[kBatch][kCompRows];
 #pragma unroll
-                        for (int l = 0; l + 1 < LEVELS; ++l) {
-                            if (l < c) {
-                                acc[l + 1] = over(acc[l + 1], acc[l]);
-                                acc[l] = zero;
-                            }
-                        }
-                    }
+        for (int u = 0; u < kBatch; ++u) {
+#pragma unroll
+            for (int r = 0; r < kCompRows; ++r) v[u][r] = zero;
+            if (pos[u] >= 0) {
+                const int b = p.order[pos[u]];
+                const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
+                const float4 *src = p.partials + p.poff[b] + (px - x0);
+#pragma unroll
+                for (int r = 0; r < kCompRows; ++r) {
+                    const int py = ty0 + threadIdx.y + kCompH * r;
+                    if (px >= x0 && px < x0 + w && py >= y0 && py < y0 + h)
+                        v[u][r] = __ldcs(src + static_cast<long long>(py - y0) * w);
                 }
             }
         }
-        if (px < p.W && py < p.H) {
-            float4 r = acc[0];
 #pragma unroll
-            for (int l = 1; l < LEVELS; ++l)
-                if (l == p.n_levels - 1) r = acc[l];
-            __stcs(p.out + static_cast<long long>(py) * p.W + px, r);
+        for (int u = 0; u < kBatch; ++u) {
+            if (pos[u] >= 0) {
+                if (LEVELS > 1 && prev >= 0) carry(carried_levels<LEVELS>(p, prev, pos[u]));
+#pragma unroll
+                for (int r = 0; r < kCompRows; ++r) acc[r][0] = over(acc[r][0], v[u][r]);
+                prev = pos[u];
+            }
+        }
+    }
+    if (LEVELS > 1 && prev >= 0) carry(carried_levels<LEVELS>(p, prev, p.nb));
+#pragma unroll
+    for (int r = 0; r < kCompRows; ++r) {
+        const int py = ty0 + threadIdx.y + kCompH * r;
+        if (px < p.W && py < p.H) {
+            // after the last carry every level but n_levels - 1 is exactly zero,
+            // and "over" with a zero operand is exact: folding all levels gives
+            // that level bit for bit, with static indices (a selected index would
+            // put the accumulators in local memory)
+            float4 res = acc[r][LEVELS - 1];
+#pragma unroll
+            for (int l = LEVELS - 2; l >= 0; --l) res = over(res, acc[r][l]);
+            __stcs(p.out + static_cast<long long>(py) * p.W + px, res);
         }
     }
 }
@@ -248,14 +305,15 @@ cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s)
 
 cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s)
 {
-    if (p.n_items <= 0) return cudaSuccess;
+    if (p.n_items + p.mask_blocks <= 0) return cudaSuccess;
+    const int grid = p.n_items + p.mask_blocks;
     const bool count = p.sample_counter != nullptr;
     const bool opc = p.opc_ratio != 1.0f;
 #define VR_MARCH(T)                                                                                     \
-    (opc ? (count ? (march_kernel<T, true, true><<<p.n_items, 128, 0, s>>>(p), 0)                       \
-                  : (march_kernel<T, false, true><<<p.n_items, 128, 0, s>>>(p), 0))                     \
-         : (count ? (march_kernel<T, true, false><<<p.n_items, 128, 0, s>>>(p), 0)                      \
-                  : (march_kernel<T, false, false><<<p.n_items, 128, 0, s>>>(p), 0)))
+    (opc ? (count ? (march_kernel<T, true, true><<<grid, 128, 0, s>>>(p), 0)                       \
+                  : (march_kernel<T, false, true><<<grid, 128, 0, s>>>(p), 0))                     \
+         : (count ? (march_kernel<T, true, false><<<grid, 128, 0, s>>>(p), 0)                      \
+                  : (march_kernel<T, false, false><<<grid, 128, 0, s>>>(p), 0)))
     switch (dtype) {
     case VR_F32: VR_MARCH(float); break;
     case VR_BF16: VR_MARCH(__nv_bfloat16); break;
@@ -287,11 +345,21 @@ cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out
     return cudaGetLastError();
 }
 
+cudaError_t launch_tile_masks(const CompositeParams &p, cudaStream_t s)
+{
+    const int tiles = p.tiles_x * p.tiles_y;
+    if (tiles <= 0) return cudaSuccess;
+    tile_mask_kernel<<<(tiles + kMaskThreads - 1) / kMaskThreads, kMaskThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s)
 {
     dim3 block(kCompW, kCompH);
-    dim3 grid((p.W + kCompW - 1) / kCompW, (p.H + kCompH * kCompRows - 1) / (kCompH * kCompRows));
+    dim3 grid(p.tiles_x, p.tiles_y);
     if (p.W <= 0 || p.H <= 0) return cudaSuccess;
+    if (p.tiles_x != (p.W + kCompW - 1) / kCompW || p.tiles_y != (p.H + kCompTileH - 1) / kCompTileH || !p.tile_mask)
+        return cudaErrorInvalidValue;
     // programmatic dependent launch: the composite's blocks may start while the
     // preceding kernel in the stream finishes (they wait in griddepcontrol.wait
     // before touching its output); after any other stream operation, or a kernel

@@ -402,7 +402,7 @@ vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int ou
     static thread_local MeshParams mp;  // ~15 KB: keep off the stack
     vr_status st = prepare_frame(ctx, &mesh->geom, ctx->frame, mp.m);
     if (st != VR_OK) return st;
-    st = ensure_frame(ctx, ctx->frame, std::max(ctx->frame.total_px, 1LL));
+    st = ensure_frame(ctx, ctx->frame, std::max(ctx->frame.pool_px, 1LL));
     if (st != VR_OK) return st;
     mp.m.partials = ctx->frame.d_part;
     mp.rec = mesh->d_rec;

@@ -23,7 +23,8 @@ namespace vr {
 namespace {
 
 // Scratch shared by every call on a device, held until the process exits:
-// [0, kTfBytes) transfer-function pairs, then the partial images (float4).
+// [0, kTfBytes) transfer-function pairs, then the composite's tile masks (one
+// 16-byte mask per 32 x 16 tile of the image), then the partial images (float4).
 constexpr size_t kScratchBytes = VR_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kTfBytes = 2 * 1024 * sizeof(float4);
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -223,7 +224,9 @@ extern "C" vr_status vr_render_frame_noalloc(const float *volume_dev, const int 
         items += L.tiles_x * ((r[3] + kTileH - 1) / kTileH);
     }
     // the frame's partial images must fit the fixed scratch
-    if (static_cast<size_t>(px) * sizeof(float4) > kScratchBytes - kTfBytes) return VR_ERR_ARG;
+    const int tiles_x = (cam->width + kCompW - 1) / kCompW, tiles_y = (cam->height + kCompTileH - 1) / kCompTileH;
+    const size_t mask_bytes = static_cast<size_t>(tiles_x) * tiles_y * sizeof(uint4);
+    if (static_cast<size_t>(px) * sizeof(float4) + mask_bytes > kScratchBytes - kTfBytes) return VR_ERR_ARG;
 
     double f[3] = {cam->dir[0], cam->dir[1], cam->dir[2]}, r[3], u[3];
     if (!normalize3(f)) return VR_ERR_ARG;
@@ -279,7 +282,8 @@ extern "C" vr_status vr_render_frame_noalloc(const float *volume_dev, const int 
     if (scratch_address(&scratch) != cudaSuccess || !scratch) return VR_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float4 *tf_dev = static_cast<float4 *>(scratch);
-    float4 *partials = reinterpret_cast<float4 *>(static_cast<unsigned char *>(scratch) + kTfBytes);
+    uint4 *masks = reinterpret_cast<uint4 *>(static_cast<unsigned char *>(scratch) + kTfBytes);
+    float4 *partials = reinterpret_cast<float4 *>(static_cast<unsigned char *>(scratch) + kTfBytes + mask_bytes);
     // pageable source: the copy has left `pairs` before cudaMemcpyAsync returns
     if (cudaMemcpyAsync(tf_dev, pairs.data(), pairs.size() * sizeof(float), cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
@@ -304,6 +308,11 @@ extern "C" vr_status vr_render_frame_noalloc(const float *volume_dev, const int 
     }
     cp.partials = partials;
     cp.out = reinterpret_cast<float4 *>(out_rgba_dev);
+    cp.tile_mask = masks;
+    cp.tiles_x = tiles_x;
+    cp.tiles_y = tiles_y;
+    cp.group[0] = 1;
+    if (launch_tile_masks(cp, s) != cudaSuccess) return VR_ERR_CUDA;
     if (launch_composite(cp, s) != cudaSuccess) return VR_ERR_CUDA;
     return VR_OK;
 }

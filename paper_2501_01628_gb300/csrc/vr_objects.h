@@ -67,7 +67,10 @@ struct vr_frame_s {
     std::vector<int> rects;        // nb x 4
     std::vector<int> order;        // nb
     std::vector<long long> poff;   // nb, float4 units
-    long long total_px = 0;
+    long long total_px = 0;        // partial pixels (float4), 128-byte aligned per brick
+    int tiles_x = 0, tiles_y = 0;  // composite tiles (kCompW x kCompTileH)
+    long long pool_px = 0;         // float4 units of the pool: partials, then one mask per tile
+    bool masks_ready = false;      // the masks were written by this frame's march
     float4 *d_part = nullptr;
     long long cap_px = 0;
     bool owned_by_ctx = false;

@@ -204,11 +204,15 @@ def _array(x, what, shape=None, ndim=None, device=None, writable=False):
     return (x.data_ptr() if is_t else x.ctypes.data), int(on_dev), x
 
 
-def _image_of(ctx, out, what="out"):
+def _camera_size(ctx):
     size = _cam_size.get(_key(ctx))
-    if size is None:
-        raise ValueError("no camera set on this context")
-    return _array(out, what, shape=size + (4,), writable=True)
+    if size is None:  # the library's own answer to a render without a camera
+        raise VrError(VR_ERR_STATE, "no camera set on this context")
+    return size
+
+
+def _image_of(ctx, out, what="out"):
+    return _array(out, what, shape=_camera_size(ctx) + (4,), writable=True)
 
 
 # --------------------------------------------------------------------------
@@ -358,9 +362,7 @@ def vr_volume_update_async(vol, volume, stream=None):
 def vr_render_backward(ctx, vol, grad_rgba, grad_tf, grad_density=None, stream=None):
     """Adds dL/d(table) to grad_tf and dL/d(voxels) to grad_density (CUDA float32
     tensors) for dL/dI = grad_rgba ([H, W, 4] CUDA float32)."""
-    size = _cam_size.get(_key(ctx))
-    if size is None:
-        raise ValueError("no camera set on this context")
+    size = _camera_size(ctx)
     g, _, _ = _array(grad_rgba, "grad_rgba", shape=size + (4,), device=True)
     t, _, _ = _array(grad_tf, "grad_tf", shape=(_tf_len.get(_key(ctx), -1), 4), device=True)
     d = None
@@ -517,7 +519,7 @@ def vr_frame_partial(frame, brick: int):
 def vr_composite(ctx, frame, out, stream=None):
     size = _frame_size.get(_key(frame))
     if size is None:
-        raise ValueError("unknown frame")
+        raise VrError(VR_ERR_ARG, "unknown frame")
     ptr, on_dev, _ = _array(out, "out", shape=size + (4,), writable=True)
     _check(lib().vr_composite(ctx, frame, ptr, on_dev, _stream(stream)), ctx, "vr_composite")
 

@@ -152,8 +152,9 @@ def test_binding_rejects_mistyped_or_misshaped_buffers_before_any_launch():
             vr.vr_render_frame_noalloc(vol, part, tf, 0.0, 1.0, cam, out)
     # context calls: the image must match the camera last set on the context
     fake = ctypes.c_void_p(0x1234)
-    with pytest.raises(ValueError, match="no camera"):
+    with pytest.raises(vr.VrError, match="no camera") as e:
         vr.vr_render_frame(fake, None, good_out)
+    assert e.value.status == vr.VR_ERR_STATE
     vr._cam_size[vr._key(fake)] = (6, 8)
     try:
         for out, msg in ((torch.zeros((6, 8, 3)), "shape"), (torch.zeros(6 * 8 * 4), "shape"),
