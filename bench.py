@@ -91,21 +91,27 @@ def source_key(sources) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(summary: str = "march_paper_workload.md",
-                     sources=("vr_kernels.cu", "vr_device.cuh", "vr_internal.h")):
-    """DRAM bytes per launch of a kernel from its committed ncu summary, if the
-    summary was taken on the current kernel code (else None)."""
+def recorded_value(field: str, summary: str = "march_paper_workload.md",
+                   sources=("vr_kernels.cu", "vr_device.cuh", "vr_internal.h")):
+    """A figure (`field: value` line) of a kernel's committed ncu summary, if
+    the summary was taken on the current kernel code (else None)."""
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
         key = source_key(sources)
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(re.escape(field) + r":\s*([0-9.eE+]+)", text)
     k = re.search(r"kernel_source_key:\s*([0-9a-f]+)", text)
     if not m or not k or k.group(1) != key:
         return None
     return float(m.group(1))
+
+
+def recorded_traffic(summary: str = "march_paper_workload.md",
+                     sources=("vr_kernels.cu", "vr_device.cuh", "vr_internal.h")):
+    """DRAM bytes per launch of a kernel from its committed ncu summary."""
+    return recorded_value("traffic_bytes_per_launch", summary, sources)
 
 
 MESH_SOURCES = ("vr_mesh.cu", "vr_mesh.h", "vr_device.cuh", "vr_internal.h")
@@ -394,6 +400,38 @@ def run_ours(a):
     samples = float(sum(counts[vi] for vi in timed_views))
     ms, e2e_s, samples = reduce_job(ms, e2e_s, samples, world)
 
+    # precision form on the same workload: bfloat16 brick storage, FP32
+    # accumulation; frame time against the f32 frames above, and the largest
+    # image difference to the f32 render of one view
+    forms = None
+    if world == 1 and a.workload == "paper":
+        vb = vr.vr_volume_create(ctx, vol, "bf16", wl["part"])
+        vr.vr_set_camera(ctx, cams[0])
+        vr.vr_render_frame(ctx, v, out)
+        ref0 = out.clone()
+        for i in range(a.warmup):
+            vr.vr_set_camera(ctx, cams[views[i]])
+            vr.vr_render_frame(ctx, vb, out)
+        nb16 = min(len(timed_views), 400)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for vi in timed_views[:nb16]:
+            vr.vr_set_camera(ctx, cams[vi])
+            vr.vr_render_frame(ctx, vb, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / nb16
+        vr.vr_set_camera(ctx, cams[0])
+        vr.vr_render_frame(ctx, vb, out)
+        diff = (out - ref0).abs()
+        fms = ms / len(timed_views)
+        forms = dict(bf16=dict(ms_per_frame=bms, frames=nb16, speedup_vs_f32=fms / bms,
+                               samples_per_s=sum(counts[vi] for vi in timed_views[:nb16]) / (bms * nb16 / 1e3),
+                               image_diff_vs_f32=dict(max=float(diff.max()), mean=float(diff.mean())),
+                               note="bfloat16 brick storage (8-byte quads), FP32 accumulation; accuracy against "
+                                    "the FP64 oracle is checked on the 1024^3 precision workload"))
+        vr.vr_volume_release(vb)
+
     # ray-state cycling on the same frames (rays carry (C, T) through the bricks,
     # global early termination): executed samples and frame time
     cyc = None
@@ -475,9 +513,10 @@ def run_ours(a):
                       note="FP32 %d flops/sample x executed samples / mean march launch; peak = %d SMs "
                            "(cudaDeviceProp.multiProcessorCount) x 128 lanes x 2 x %.0f MHz (derived)"
                            % (FLOPS_PER_SAMPLE, sms, sm_max)),
-        roofline_l1=dict(note="ncu on the march: L1 data-pipe LSU wavefronts 74% of peak, issue slots "
-                              "61%, top stall long scoreboard; L1 hit 78%, L2 hit 32% of the L1 misses, "
-                              "DRAM traffic = compulsory quad bytes"),
+        roofline_l1=dict(frac=recorded_value("l1_wavefronts_frac") if a.workload == "paper" else None,
+                         unit="fraction of peak L1 data-pipe wavefronts",
+                         note="ncu --set full on the march of this kernel code (null once the code changes): "
+                              "the L1/shared data pipe is the march's closest bound; see profiles/"),
         roofline_hbm=dict(march=dict(achieved=march_hbm_gbs, peak=hbm, unit="GB/s", frac=march_hbm_gbs / hbm,
                                      note="compulsory bytes (volume once + partial writes) / march time, %s"
                                           % hbm_src),
@@ -489,7 +528,10 @@ def run_ours(a):
         cpu_baseline=cpu,
         e2e=dict(value=samples / e2e_s, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=W * H * 16,
                  note="vr_render_frame into pinned host memory: render + %.1f MB device-to-host copy + wait "
-                      "per frame; the per-step host inputs are the camera (kernel parameters)" % (W * H * 16 / 1e6)),
+                      "per frame. h2d_bytes_per_step is 0 by design: the volume is resident library state and "
+                      "the one per-step input, the camera, travels as kernel parameters (no copy)"
+                      % (W * H * 16 / 1e6)),
+        forms=forms,
     )
     print(json.dumps(line))
 

@@ -525,10 +525,18 @@ vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s)
     if (nf > 0 && !radix)
         return fail(ctx, VR_ERR_ARG, "composite schedule factors do not multiply to the brick count");
     cp.n_levels = radix ? nf : 1;
-    // group[l]: partials per level-l group of the association tree
-    cp.group[0] = 1;
-    for (int l = 1; l < cp.n_levels; ++l) cp.group[l] = cp.group[l - 1] * ctx->factors[l - 1];
+    // gid[q]: the group of visibility position q at each level l >= 1 of the
+    // association tree (groups of factors[0] x ... x factors[l-1] positions)
     for (int j = 0; j < fr.nb; ++j) cp.order[j] = fr.order[j];
+    for (int q = 0; q <= fr.nb; ++q) {
+        unsigned long long g = 0;
+        long long size = 1;
+        for (int l = 1; l < cp.n_levels; ++l) {
+            size *= ctx->factors[l - 1];
+            g |= static_cast<unsigned long long>((q / size) & 0xff) << (8 * (l - 1));
+        }
+        cp.gid[q] = g;
+    }
     for (int b = 0; b < fr.nb; ++b) {
         std::memcpy(cp.rect[b], &fr.rects[4 * b], 4 * sizeof(int));
         cp.poff[b] = fr.poff[b];

@@ -90,7 +90,8 @@ struct CompositeParams {
     int nb;
     int n_levels;                     // 1 = direct
     int order[kMaxBricks];            // brick ids front to back
-    int group[kMaxFactors];           // radix-k: group[l] = f_0 f_1 ... f_{l-1} partials per level-l group
+    unsigned long long gid[kMaxBricks + 1];   // radix-k: byte l-1 = group index of position q at level l
+                                              // (entry nb: one past the last group at every level)
     int rect[kMaxBricks][4];          // by brick id
     long long poff[kMaxBricks];       // by brick id
     const float4 *partials;

@@ -133,7 +133,13 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     const float4 c =
         dev::march_run<S, COUNT, OPC>(p.data, B, run, p.tf, p.tf_scale, p.tf_bias, p.ntf, p.ert_T, executed, p.opc_ratio,
                                       p.count_error);
-    p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = c;
+    // the composite reads the partial next: keep it in L2 ahead of the streamed bricks
+    float4 *dst = p.partials + B.poff + static_cast<long long>(ry) * B.rect[2] + rx;
+    unsigned long long policy;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "f"(c.x), "f"(c.y),
+                 "f"(c.z), "f"(c.w), "l"(policy)
+                 : "memory");
     if (COUNT && executed) atomicAdd(p.sample_counter, executed);
 }
 
@@ -169,118 +175,109 @@ __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Composite: one 32x8-thread block per kCompW x kCompTileH image tile, one
-// thread per pixel of each of the tile's kCompRows 32x8 slabs; partials are
+// Composite: one 32x8-thread block per kCompW x kCompTileH image tile; the
+// tile's kCompRows 32x8 slabs in turn, one thread per pixel. Partials are
 // combined front to back with "over" along the configured association tree.
 // ---------------------------------------------------------------------------
 // The tile's mask (one 16-byte load, the same for the whole block) lists the
-// visibility positions of the bricks that overlap it. Absent partials are the
-// identity of "over", so only the association tree's carries at skipped
-// positions matter, and consecutive carries compose to the deepest one: before
-// the brick at position j, after the previous listed position i, the levels
-// completed anywhere in [i, j) are merged. Level l (>= 1) completes after
-// position q when (q + 1) is a multiple of group[l], so the deepest level
-// completed in [i, j) is the largest l with j / group[l] != i / group[l].
-// Partial loads for up to kBatch listed bricks and all kCompRows pixels are
-// issued before any is combined.
-template <int LEVELS>
+// visibility positions of the bricks that overlap it, so no block compacts a
+// brick list of its own. Partial loads of four listed bricks are in flight
+// together. Absent partials are the identity of "over", so only the tree's
+// carries at skipped positions matter, and consecutive carries compose to the
+// deepest one: before the brick at position j, after the previous listed
+// position i, every level whose group changes between i and j is merged.
+
+// The deepest level of the association tree whose group changes between
+// visibility positions i < j: gid[q] holds q's group index at level l (groups
+// of factors[0] x ... x factors[l-1] positions) in byte l - 1, so it is the
+// highest byte in which gid[i] and gid[j] differ (0: none -- same level-1 group).
 __device__ __forceinline__ int carried_levels(const CompositeParams &p, int i, int j)
 {
-    int c = 0;
-#pragma unroll
-    for (int l = 1; l < LEVELS; ++l)
-        if (l < p.n_levels && j / p.group[l] != i / p.group[l]) c = l;
-    return c;
+    const unsigned long long x = p.gid[i] ^ p.gid[j];
+    return x ? (71 - __clzll(static_cast<long long>(x))) >> 3 : 0;
+}
+
+// next listed position (-1 when none is left)
+__device__ __forceinline__ int next_pos(unsigned long long &r0, unsigned long long &r1)
+{
+    int q = -1;
+    if (r0) {
+        q = __ffsll(static_cast<long long>(r0)) - 1;
+        r0 &= r0 - 1;
+    } else if (r1) {
+        q = 63 + __ffsll(static_cast<long long>(r1));
+        r1 &= r1 - 1;
+    }
+    return q;
 }
 
 template <int LEVELS>
 __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ CompositeParams p)
 {
     constexpr int kBatch = 4;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const int tx0 = blockIdx.x * kCompW, ty0 = blockIdx.y * kCompTileH;
     const int px = tx0 + threadIdx.x;
     // launched as a programmatic dependent of the march: wait for the preceding
     // grid's completion and memory (the masks and partials are its output)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint4 mk = __ldg(p.tile_mask + blockIdx.y * p.tiles_x + blockIdx.x);
-    // positions not yet combined: 0-63 in rest0, 64-127 in rest1
-    unsigned long long rest0 = static_cast<unsigned long long>(mk.x) | (static_cast<unsigned long long>(mk.y) << 32);
-    unsigned long long rest1 = static_cast<unsigned long long>(mk.z) | (static_cast<unsigned long long>(mk.w) << 32);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 acc[kCompRows][LEVELS];
+    for (int half = 0; half < kCompRows; ++half) {
+        const int py = ty0 + threadIdx.y + kCompH * half;
+        unsigned long long r0 = static_cast<unsigned long long>(mk.x) | (static_cast<unsigned long long>(mk.y) << 32);
+        unsigned long long r1 = static_cast<unsigned long long>(mk.z) | (static_cast<unsigned long long>(mk.w) << 32);
+        float4 acc[LEVELS];
 #pragma unroll
-    for (int r = 0; r < kCompRows; ++r)
+        for (int l = 0; l < LEVELS; ++l) acc[l] = zero;
+        int prev = -1;
+        while (r0 | r1) {
+            int pos[kBatch];
+            float4 v[kBatch];
 #pragma unroll
-        for (int l = 0; l < LEVELS; ++l) acc[r][l] = zero;
-    // merge the c lowest levels upwards, acc[r][l + 1] <- acc[r][l + 1] over acc[r][l]
-    auto carry = [&](int c) {
-#pragma unroll
-        for (int r = 0; r < kCompRows; ++r)
-#pragma unroll
-            for (int l = 0; l + 1 < LEVELS; ++l) {
-                const bool m = l < c;
-                const float4 merged = over(acc[r][l + 1], acc[r][l]);
-                acc[r][l + 1] = m ? merged : acc[r][l + 1];
-                acc[r][l] = m ? zero : acc[r][l];
-            }
-    };
-    int prev = -1;  // visibility position of the last brick combined
-    for (;;) {
-        int pos[kBatch];
-        int cnt = 0;
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            pos[u] = -1;
-            if (rest0) {
-                pos[u] = __ffsll(static_cast<long long>(rest0)) - 1;
-                rest0 &= rest0 - 1;
-                ++cnt;
-            } else if (rest1) {
-                pos[u] = 63 + __ffsll(static_cast<long long>(rest1));
-                rest1 &= rest1 - 1;
-                ++cnt;
-            }
-        }
-        if (cnt == 0) break;
-        float4 v[kBatch][kCompRows];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-#pragma unroll
-            for (int r = 0; r < kCompRows; ++r) v[u][r] = zero;
-            if (pos[u] >= 0) {
-                const int b = p.order[pos[u]];
-                const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
-                const float4 *src = p.partials + p.poff[b] + (px - x0);
-#pragma unroll
-                for (int r = 0; r < kCompRows; ++r) {
-                    const int py = ty0 + threadIdx.y + kCompH * r;
+            for (int u = 0; u < kBatch; ++u) {
+                pos[u] = next_pos(r0, r1);
+                v[u] = zero;
+                if (pos[u] >= 0) {
+                    const int b = p.order[pos[u]];
+                    const int x0 = p.rect[b][0], y0 = p.rect[b][1], w = p.rect[b][2], h = p.rect[b][3];
                     if (px >= x0 && px < x0 + w && py >= y0 && py < y0 + h)
-                        v[u][r] = __ldcs(src + static_cast<long long>(py - y0) * w);
+                        v[u] = __ldcs(p.partials + p.poff[b] + static_cast<long long>(py - y0) * w + (px - x0));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (pos[u] >= 0) {
+                    if (LEVELS > 1 && prev >= 0) {
+                        const int c = carried_levels(p, prev, pos[u]);
+#pragma unroll
+                        for (int l = 0; l + 1 < LEVELS; ++l)
+                            if (l < c) {
+                                acc[l + 1] = over(acc[l + 1], acc[l]);
+                                acc[l] = zero;
+                            }
+                    }
+                    acc[0] = over(acc[0], v[u]);
+                    prev = pos[u];
                 }
             }
         }
+        if (LEVELS > 1 && prev >= 0) {
+            const int c = carried_levels(p, prev, p.nb);
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            if (pos[u] >= 0) {
-                if (LEVELS > 1 && prev >= 0) carry(carried_levels<LEVELS>(p, prev, pos[u]));
-#pragma unroll
-                for (int r = 0; r < kCompRows; ++r) acc[r][0] = over(acc[r][0], v[u][r]);
-                prev = pos[u];
-            }
+            for (int l = 0; l + 1 < LEVELS; ++l)
+                if (l < c) {
+                    acc[l + 1] = over(acc[l + 1], acc[l]);
+                    acc[l] = zero;
+                }
         }
-    }
-    if (LEVELS > 1 && prev >= 0) carry(carried_levels<LEVELS>(p, prev, p.nb));
-#pragma unroll
-    for (int r = 0; r < kCompRows; ++r) {
-        const int py = ty0 + threadIdx.y + kCompH * r;
         if (px < p.W && py < p.H) {
             // after the last carry every level but n_levels - 1 is exactly zero,
             // and "over" with a zero operand is exact: folding all levels gives
             // that level bit for bit, with static indices (a selected index would
             // put the accumulators in local memory)
-            float4 res = acc[r][LEVELS - 1];
+            float4 res = acc[LEVELS - 1];
 #pragma unroll
-            for (int l = LEVELS - 2; l >= 0; --l) res = over(res, acc[r][l]);
+            for (int l = LEVELS - 2; l >= 0; --l) res = over(res, acc[l]);
             __stcs(p.out + static_cast<long long>(py) * p.W + px, res);
         }
     }
@@ -355,15 +352,12 @@ cudaError_t launch_tile_masks(const CompositeParams &p, cudaStream_t s)
 
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s)
 {
+    if (p.W <= 0 || p.H <= 0) return cudaSuccess;
+    if (p.tiles_x != (p.W + kCompW - 1) / kCompW || p.tiles_y != (p.H + kCompTileH - 1) / kCompTileH ||
+        !p.tile_mask)
+        return cudaErrorInvalidValue;
     dim3 block(kCompW, kCompH);
     dim3 grid(p.tiles_x, p.tiles_y);
-    if (p.W <= 0 || p.H <= 0) return cudaSuccess;
-    if (p.tiles_x != (p.W + kCompW - 1) / kCompW || p.tiles_y != (p.H + kCompTileH - 1) / kCompTileH || !p.tile_mask)
-        return cudaErrorInvalidValue;
-    // programmatic dependent launch: the composite's blocks may start while the
-    // preceding kernel in the stream finishes (they wait in griddepcontrol.wait
-    // before touching its output); after any other stream operation, or a kernel
-    // that never signals, this is ordinary stream order
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -374,9 +368,14 @@ cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s)
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (p.n_levels <= 1) return cudaLaunchKernelEx(&cfg, composite_kernel<1>, p);
-    if (p.n_levels <= 4) return cudaLaunchKernelEx(&cfg, composite_kernel<4>, p);
-    return cudaLaunchKernelEx(&cfg, composite_kernel<kMaxFactors>, p);
+    switch (p.n_levels) {  // accumulators for exactly the tree's depth (registers bound the occupancy)
+    case 0:
+    case 1: return cudaLaunchKernelEx(&cfg, composite_kernel<1>, p);
+    case 2: return cudaLaunchKernelEx(&cfg, composite_kernel<2>, p);
+    case 3: return cudaLaunchKernelEx(&cfg, composite_kernel<3>, p);
+    case 4: return cudaLaunchKernelEx(&cfg, composite_kernel<4>, p);
+    default: return cudaLaunchKernelEx(&cfg, composite_kernel<kMaxFactors>, p);
+    }
 }
 
 }  // namespace vr

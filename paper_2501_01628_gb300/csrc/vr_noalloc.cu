@@ -311,7 +311,6 @@ extern "C" vr_status vr_render_frame_noalloc(const float *volume_dev, const int 
     cp.tile_mask = masks;
     cp.tiles_x = tiles_x;
     cp.tiles_y = tiles_y;
-    cp.group[0] = 1;
     if (launch_tile_masks(cp, s) != cudaSuccess) return VR_ERR_CUDA;
     if (launch_composite(cp, s) != cudaSuccess) return VR_ERR_CUDA;
     return VR_OK;
