@@ -15,6 +15,10 @@ Parity pins (checked in ``tests/test_oracle_pins.py``):
   P5 exact trilinear weights on the axis-aligned 64^3 / 256^2 lattice with a
      linear ramp volume (closed form)
   P6 range / alpha-0 / alpha-1 / identity invariants
+  16-bit storage: every f16 / bf16 code decodes to its IEEE-754 value
+  (numpy float16; float32 with the code in the top half)
+  cameras: pixel rays meet the image plane on square cells on non-square
+  images (fixes the W/H aspect factor of the perspective rays)
 Mesh pins (``tests/test_oracle_mesh.py``): linear fields reproduced exactly,
 barycentric partition of unity and containment, bins equal brute force, mesh
 renders equal the pinned voxel renders on rays along shared grid lines, the
