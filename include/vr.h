@@ -190,6 +190,19 @@ vr_status vr_set_host_output_async(vr_ctx ctx, int on);
  * not depend on it; the speed does (it sets how compactly a warp's rays touch
  * the brick's cache lines). */
 vr_status vr_set_packet_width(vr_ctx ctx, int packet_width);
+/* March variant for float32 volumes (off by default). With on != 0, volumes
+ * created afterwards also keep a scalar copy of their bricks (one float per
+ * haloed voxel, about a quarter of the xy-quad storage), and the march of
+ * those volumes stages the brick voxels of each 8x16-pixel tile in shared
+ * memory, slab by slab in depth (bulk asynchronous copies, cp.async.bulk,
+ * completing on an mbarrier, two stages per block), instead of reading
+ * xy-quads through L1. The image is the same bit for bit; the speed differs
+ * (the benchmark spec's staging of brick tiles for ray packets; measured against the
+ * xy-quad march on the orbit workload). Volumes without the scalar copy (other
+ * storage types, or created while staging was off) keep the xy-quad march.
+ * Each bounded wait for a staged slab that gives up makes the next vr_sync
+ * return VR_ERR_TIMEOUT. */
+vr_status vr_set_march_staging(vr_ctx ctx, int on);
 /* Frame algorithm of vr_render_frame.
  *   0 (default): sort-last -- one partial image per brick, then the "over"
  *     composite (the steps above).

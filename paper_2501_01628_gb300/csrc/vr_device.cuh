@@ -387,6 +387,34 @@ __device__ __forceinline__ float4 march_run(const void *data, const BrickLaunch 
     return make_float4(C0, C1, C2, 1.0f - T);
 }
 
+// ---------------------------------------------------------------------------
+// Composite tile masks: one thread per composite tile (kCompW x kCompTileH
+// pixels) sets bit j of its 128-bit mask when the brick at visibility position
+// j has a non-empty footprint rectangle that overlaps the tile. Every thread
+// walks the positions in the same order, so the rectangle reads are uniform
+// across the warp (broadcast, not per-lane gathers).
+// ---------------------------------------------------------------------------
+template <typename RectOf>
+__device__ __forceinline__ void write_tile_mask(int tile, int tiles_x, int tiles_y, int nb, const int *order,
+                                                RectOf rect_of, uint4 *mask)
+{
+    if (tile >= tiles_x * tiles_y) return;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int x0 = tx * kCompW, y0 = ty * kCompTileH;
+    unsigned long long lo = 0, hi = 0;
+    for (int j = 0; j < nb; ++j) {
+        const int4 r = rect_of(order[j]);
+        const bool ov = r.z > 0 && r.w > 0 && r.x < x0 + kCompW && x0 < r.x + r.z && r.y < y0 + kCompTileH &&
+                        y0 < r.y + r.w;
+        if (ov) {
+            if (j < 64) lo |= 1ull << j;
+            else hi |= 1ull << (j - 64);
+        }
+    }
+    mask[tile] = make_uint4(static_cast<unsigned>(lo), static_cast<unsigned>(lo >> 32), static_cast<unsigned>(hi),
+                            static_cast<unsigned>(hi >> 32));
+}
+
 __device__ __forceinline__ float4 over(float4 front, float4 back)
 {
     const float w = 1.0f - front.w;

@@ -347,13 +347,28 @@ cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
             B.s[a] = bx[3 + a] - bx[a] + 2;
         }
         B.block_begin = static_cast<int>(blocks);
-        B.pad = 0;
+        B.row = 0;
         blocks += (B.quads + kPackChunk - 1) / kPackChunk;
     }
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     pp.n_blocks = static_cast<int>(blocks);
     if (fault_now(VR_FAULT_LAUNCH)) return cudaErrorLaunchFailure;
-    return launch_pack(pp, vol->dtype, s);
+    cudaError_t e = launch_pack(pp, vol->dtype, s);
+    if (e != cudaSuccess || !vol->d_scalar) return e;
+    // the staged march's scalar copy
+    blocks = 0;
+    for (int b = 0; b < nb; ++b) {
+        PackBrick &B = pp.b[b];
+        B.dst = vol->d_scalar + vol->sbase[b];
+        B.row = vol->sxp[b];
+        B.quads = static_cast<long long>(B.row) * B.s[1] * B.s[2];
+        B.block_begin = static_cast<int>(blocks);
+        blocks += (B.quads + kPackChunk - 1) / kPackChunk;
+    }
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    pp.n_blocks = static_cast<int>(blocks);
+    if (fault_now(VR_FAULT_LAUNCH)) return cudaErrorLaunchFailure;
+    return launch_scalar_pack(pp, s);
 }
 
 vr_status ensure_frame(vr_ctx ctx, vr_frame_s &fr, long long px)
@@ -505,7 +520,17 @@ vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s)
     mp.mask_tiles_y = fr.tiles_y;
     mp.mask_blocks = (fr.tiles_x * fr.tiles_y + kMaskThreads - 1) / kMaskThreads;
     const int t = timing_begin(ctx, 0, s);
-    VR_LAUNCH(ctx, launch_march(mp, vol->dtype, s));
+    if (ctx->staging && vol->d_scalar) {
+        static thread_local StagedBricks sb;
+        sb.scalar = vol->d_scalar;
+        for (size_t b = 0; b < vol->sbase.size(); ++b) {
+            sb.sbase[b] = vol->sbase[b];
+            sb.sxp[b] = vol->sxp[b];
+        }
+        VR_LAUNCH(ctx, launch_march_staged(mp, sb, s));
+    } else {
+        VR_LAUNCH(ctx, launch_march(mp, vol->dtype, s));
+    }
     timing_end(ctx, t, s);
     fr.masks_ready = true;
     return VR_OK;
@@ -807,9 +832,10 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
     if (err) {
         VR_CUDA(ctx, cudaMemset(ctx->d_error, 0, sizeof(int)));
         if (err & 2) return fail(ctx, VR_ERR_TIMEOUT, "a bounded device-side wait of the batched kernel gave up");
+        if (err & 32) return fail(ctx, VR_ERR_TIMEOUT, "a bounded wait for a staged brick slab gave up");
         if (err & 8) return fail(ctx, VR_ERR_BOUNDS, "a mesh point location found no element");
         if (err & 16)
-            return fail(ctx, VR_ERR_BOUNDS, "a counted sample's quad index fell outside its brick's storage");
+            return fail(ctx, VR_ERR_BOUNDS, "a counted sample's cell fell outside its brick's storage or staged box");
         return fail(ctx, VR_ERR_BOUNDS, "a backward pass met an owned-sample run longer than 4096 samples");
     }
     return VR_OK;
@@ -850,6 +876,26 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VR_CUDA(ctx, vr::host::dev_malloc(&vol->d_data, static_cast<size_t>(off_bytes)));
     vol->bytes = off_bytes;
+    if (ctx->staging && storage == VR_F32) {
+        // scalar copy for the staged march: rows padded to 4 elements (16 bytes),
+        // each brick 128-byte aligned
+        long long off = 0;
+        vol->sbase.resize(nb);
+        vol->sxp.resize(nb);
+        for (int b = 0; b < nb; ++b) {
+            const int *bx = &vol->boxes[6 * b];
+            vol->sxp[b] = (bx[3] - bx[0] + 2 + 3) & ~3;
+            vol->sbase[b] = off;
+            off += static_cast<long long>(vol->sxp[b]) * (bx[4] - bx[1] + 2) * (bx[5] - bx[2] + 2);
+            off = (off + 31) & ~31LL;
+        }
+        const cudaError_t es2 = vr::host::dev_malloc(&vol->d_scalar, static_cast<size_t>(off) * sizeof(float));
+        if (es2 != cudaSuccess) {
+            cudaFree(vol->d_data);
+            return cuda_fail(ctx, es2, "scalar brick copy");
+        }
+        vol->bytes += off * static_cast<long long>(sizeof(float));
+    }
     const float *dsrc = src;
     float *tmp = nullptr;
     const size_t nvox = static_cast<size_t>(dims[0]) * dims[1] * dims[2];
@@ -859,6 +905,7 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
         if (e != cudaSuccess) {
             cudaFree(tmp);
             cudaFree(vol->d_data);
+            cudaFree(vol->d_scalar);
             return cuda_fail(ctx, e, "volume upload");
         }
         dsrc = tmp;
@@ -868,6 +915,7 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
         cudaFree(vol->d_data);
+        cudaFree(vol->d_scalar);
         return cuda_fail(ctx, e, "volume pack");
     }
     ctx->live_objects++;
@@ -977,6 +1025,7 @@ vr_status vr_volume_release(vr_volume vol)
     DeviceGuard g(vol->ctx->device);
     cudaFree(vol->d_data);
     cudaFree(vol->d_staging);
+    cudaFree(vol->d_scalar);
     vol->ctx->live_objects--;
     delete vol;
     return VR_OK;
@@ -1185,6 +1234,13 @@ vr_status vr_set_host_output_async(vr_ctx ctx, int on)
 {
     if (!ctx) return VR_ERR_ARG;
     ctx->host_async = on != 0;
+    return VR_OK;
+}
+
+vr_status vr_set_march_staging(vr_ctx ctx, int on)
+{
+    if (!ctx) return VR_ERR_ARG;
+    ctx->staging = on != 0;
     return VR_OK;
 }
 

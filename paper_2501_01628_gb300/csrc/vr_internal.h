@@ -184,7 +184,7 @@ struct PackBrick {
     int lo[3];             // voxel box origin
     int s[3];              // haloed extents (the brick stores (s0-1)(s1-1)s2 quads)
     int block_begin;       // first block of this brick
-    int pad;
+    int row;               // scalar copies: padded row length in elements (multiple of 4)
 };
 struct PackParams {
     const float *src;      // x-fastest float32 volume
@@ -192,6 +192,16 @@ struct PackParams {
     int nb;
     int n_blocks;
     PackBrick b[kMaxBricks];
+};
+
+// Staged march (vr_staged.cu): scalar copies of the bricks, haloed, rows padded
+// to a multiple of 4 elements; kStageCap floats per shared-memory stage (two
+// stages per block).
+constexpr int kStageCap = 4096;
+struct StagedBricks {
+    const float *scalar;          // all bricks' scalar copies
+    long long sbase[kMaxBricks];  // element offset of each brick (a multiple of 32)
+    int sxp[kMaxBricks];          // padded row length (elements)
 };
 
 // Launchers (vr_kernels.cu). They return the launch's cudaError_t.
@@ -206,5 +216,8 @@ cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, vr_dtype 
 // Persistent batched kernel: cooperative launch of `blocks` blocks of 128 threads.
 cudaError_t launch_batch(const BatchParams &p, vr_dtype dtype, int blocks, cudaStream_t s);
 int batch_max_blocks_per_sm(vr_dtype dtype);
+// Staged march and the scalar brick pack (vr_staged.cu).
+cudaError_t launch_march_staged(const MarchParams &p, const StagedBricks &sb, cudaStream_t s);
+cudaError_t launch_scalar_pack(const PackParams &p, cudaStream_t s);
 
 }  // namespace vr

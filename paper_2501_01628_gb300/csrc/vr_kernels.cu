@@ -60,38 +60,10 @@ __global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ PackP
     }
 }
 
-// ---------------------------------------------------------------------------
-// Composite tile masks: one thread per composite tile (kCompW x kCompTileH
-// pixels) sets bit j of its 128-bit mask when the brick at visibility position
-// j has a non-empty footprint rectangle that overlaps the tile. Every thread
-// walks the positions in the same order, so the rectangle reads are uniform
-// across the warp (broadcast, not per-lane gathers).
-// ---------------------------------------------------------------------------
-template <typename RectOf>
-__device__ __forceinline__ void write_tile_mask(int tile, int tiles_x, int tiles_y, int nb, const int *order,
-                                                RectOf rect_of, uint4 *mask)
-{
-    if (tile >= tiles_x * tiles_y) return;
-    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const int x0 = tx * kCompW, y0 = ty * kCompTileH;
-    unsigned long long lo = 0, hi = 0;
-    for (int j = 0; j < nb; ++j) {
-        const int4 r = rect_of(order[j]);
-        const bool ov = r.z > 0 && r.w > 0 && r.x < x0 + kCompW && x0 < r.x + r.z && r.y < y0 + kCompTileH &&
-                        y0 < r.y + r.w;
-        if (ov) {
-            if (j < 64) lo |= 1ull << j;
-            else hi |= 1ull << (j - 64);
-        }
-    }
-    mask[tile] = make_uint4(static_cast<unsigned>(lo), static_cast<unsigned>(lo >> 32), static_cast<unsigned>(hi),
-                            static_cast<unsigned>(hi >> 32));
-}
-
 // Stand-alone mask pass, for frames whose march does not write the masks.
 __global__ void __launch_bounds__(kMaskThreads) tile_mask_kernel(const __grid_constant__ CompositeParams p)
 {
-    write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.tiles_x, p.tiles_y, p.nb, p.order,
+    dev::write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.tiles_x, p.tiles_y, p.nb, p.order,
                     [&](int b) { return make_int4(p.rect[b][0], p.rect[b][1], p.rect[b][2], p.rect[b][3]); },
                     p.tile_mask);
 }
@@ -110,7 +82,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     // grid has completed
     asm volatile("griddepcontrol.launch_dependents;");
     if (static_cast<int>(blockIdx.x) < p.mask_blocks) {  // the composite's tile masks
-        write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.mask_tiles_x, p.mask_tiles_y, p.nb, p.order,
+        dev::write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.mask_tiles_x, p.mask_tiles_y, p.nb, p.order,
                         [&](int b) { return make_int4(p.b[b].rect[0], p.b[b].rect[1], p.b[b].rect[2],
                                                       p.b[b].rect[3]); },
                         p.tile_mask);

@@ -92,6 +92,7 @@ struct vr_ctx_s {
     int mode = 0;                  // 0: sort-last partials + composite; 1: ray-state cycling
     float opc_ref = 0.0f;          // opacity-correction reference step in voxels (0: off)
     int packet_width = 4;          // ray packet of the march: pw x (32/pw) pixels per warp
+    bool staging = false;          // march float32 volumes with brick slabs staged in shared memory
     unsigned long long *d_counter = nullptr;
     int *d_error = nullptr;        // device error word (vr_sync reports and clears it)
     bool count_samples = false;
@@ -129,6 +130,12 @@ struct vr_volume_s {
     void *d_data = nullptr;
     long long bytes = 0;
     float *d_staging = nullptr;    // float32 source for asynchronous re-packs from host memory
+    // scalar copy of the bricks for the staged march (float32 volumes created
+    // while the context's staging was on): per brick, haloed voxels with rows
+    // padded to sxp elements, starting at element sbase
+    float *d_scalar = nullptr;
+    std::vector<long long> sbase;
+    std::vector<int> sxp;
 };
 
 namespace vr {

@@ -39,7 +39,7 @@ EXPORTS = (
     "vr_batch_autotune", "vr_batch_release", "vr_batch_configure", "vr_set_render_mode",
     "vr_set_opacity_correction", "vr_volume_update_async", "vr_set_packet_width",
     "vr_set_host_output_async", "vr_mesh_create", "vr_mesh_release", "vr_mesh_info",
-    "vr_render_mesh_frame", "vr_debug_inject_fault", "vr_batch_debug_wait",
+    "vr_render_mesh_frame", "vr_debug_inject_fault", "vr_batch_debug_wait", "vr_set_march_staging",
 )
 
 
@@ -103,6 +103,7 @@ _SIG = {
     "vr_set_render_mode": (_I, [_P, _I]),
     "vr_set_opacity_correction": (_I, [_P, ctypes.c_float]),
     "vr_set_packet_width": (_I, [_P, _I]),
+    "vr_set_march_staging": (_I, [_P, _I]),
     "vr_set_host_output_async": (_I, [_P, _I]),
     "vr_render_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
@@ -451,6 +452,12 @@ def vr_set_host_output_async(ctx, on: bool):
 def vr_set_packet_width(ctx, packet_width: int):
     """Warp ray packet packet_width x (32/packet_width) pixels (4, 8 or 16)."""
     _check(lib().vr_set_packet_width(ctx, int(packet_width)), ctx, "vr_set_packet_width")
+
+
+def vr_set_march_staging(ctx, on: bool):
+    """Float32 volumes created afterwards keep a scalar brick copy and march with
+    brick slabs staged in shared memory (same image, different speed)."""
+    _check(lib().vr_set_march_staging(ctx, int(bool(on))), ctx, "vr_set_march_staging")
 
 
 def vr_set_render_mode(ctx, mode: int):
