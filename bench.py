@@ -52,6 +52,9 @@ def args_parse():
     ap.add_argument("--workload", default="paper",
                     choices=["paper", "small", "precision", "grad", "batch", "stream", "mesh"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split", default="views", choices=["views", "bricks"],
+                    help="multi-GPU: replicas over views (weak scaling) or bricks as ranks with a radix-k "
+                         "image exchange (strong scaling)")
     return ap.parse_args()
 
 
@@ -992,8 +995,112 @@ def run_mesh(a):
     print(json.dumps(line))
 
 
+def prime_factors(n: int):
+    out, f = [], 2
+    while n > 1:
+        while n % f == 0:
+            out.append(f)
+            n //= f
+        f += 1
+    return out or [1]
+
+
+def run_bricks(a):
+    """Bricks as ranks: each rank holds a share of the 36 bricks (kd split of
+    the partition), marches it, and the ranks' images are composited by a
+    radix-k exchange over NCCL (factors: the prime factors of the rank count)
+    and gathered on rank 0. One step = one composited frame of the whole
+    volume; the work per frame is fixed as ranks are added (strong scaling).
+    value = executed samples of all ranks per second."""
+    import socket
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    else:  # one rank: a single-process group, so the same code path runs
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", str(sk.getsockname()[1]))
+        dist.init_process_group("gloo", rank=0, world_size=1)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    dist.barrier()
+    from paper_2501_01628_gb300 import sharded, vr
+    wl = workload(a.workload)
+    vol, tf = wl["vol"], wl["tf"]
+    lo, hi = float(vol.min()), float(vol.max())
+    cams = wl["cams"]
+    ctx = vr.vr_create(local)
+    vr.vr_set_transfer_function(ctx, tf, lo, hi)
+    vr.vr_set_render_params(ctx, wl["step"], wl["ert"])
+    vr.vr_set_composite_schedule(ctx, wl["schedule"])  # each rank's own bricks (empty partials elsewhere)
+    factors = prime_factors(world)
+    r = sharded.ShardedRenderer(ctx, torch.from_numpy(vol).cuda(), wl["part"], factors=factors)
+    W, H = cams[0]["width"], cams[0]["height"]
+    frame = torch.empty((H, W, 4), device="cuda") if rank == 0 else None
+    counts = []
+    vr.vr_set_count_samples(ctx, True)
+    for cam in cams:
+        r.render(cam, frame)
+        counts.append(vr.vr_get_sample_count(ctx))
+    vr.vr_set_count_samples(ctx, False)
+    for i in range(a.warmup):
+        r.render(cams[i % len(cams)], frame)
+    torch.cuda.synchronize()
+    dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0.record(stream)
+    for i in range(a.steps):
+        r.render(cams[(a.warmup + i) % len(cams)], frame)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    # end to end: the same frames, each read back to pinned host memory on rank 0
+    host = torch.empty((H, W, 4)).pin_memory() if rank == 0 else None
+    dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        out = r.render(cams[(a.warmup + i) % len(cams)], frame)
+        if rank == 0:
+            host.copy_(out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    samples = float(sum(counts[(a.warmup + i) % len(cams)] for i in range(a.steps)))
+    ms, e2e_s, samples = reduce_job(ms, e2e_s, samples, world, device="cuda" if world > 1 else "cpu")
+    r.close()
+    vr.vr_destroy(ctx)
+    dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = dict(metric=METRIC, value=samples / (ms / 1e3), unit=UNIT, n_gpus=world, steps=a.steps,
+                warmup=a.warmup, ms_per_step=ms / a.steps, higher_is_better=True, scaling="strong",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=wl["name"], parallelism="bricks as ranks, radix-k %s over %s"
+                            % ("x".join(map(str, factors)), "NCCL" if world > 1 else "one rank"),
+                            l2="inputs larger than L2" if vol.nbytes > 129e6 else "fits in L2"),
+                frames_per_s=a.steps / (ms / 1e3),
+                gpu_launches=a.steps * (2 + (len(factors) if world > 1 else 0)), clocks=clk,
+                e2e=dict(value=samples / e2e_s, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=W * H * 16,
+                         note="frame gathered on rank 0 and copied to pinned host memory"))
+    print(json.dumps(line))
+
+
 def main():
     a = args_parse()
+    if a.split == "bricks":
+        run_bricks(a)
+        return
     if a.workload == "mesh":
         run_mesh(a)
         return

@@ -146,6 +146,17 @@ vr_status vr_sync(vr_ctx ctx, void *stream);
 vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage,
                            const vr_partition *part, const float *src, int src_on_device,
                            void *stream, vr_volume *out);
+/* A rank's share of a volume (Sec. 2.2: the data is spatially distributed,
+ * each rank holding a share; Sec. 4: shares may be uneven): as
+ * vr_volume_create, but only the n_held bricks listed in `held` (distinct
+ * brick ids of `part`) are stored, packed and marched. Bricks not held render
+ * as empty partials -- the identity of "over" -- so vr_render_frame gives this
+ * rank's image: its bricks composited front to back. `src` is still the whole
+ * volume (only the held bricks and their halos are read). Shares cannot be
+ * batched (vr_batch_create returns VR_ERR_ARG). */
+vr_status vr_volume_create_share(vr_ctx ctx, const int dims[3], vr_dtype storage, const vr_partition *part,
+                                 int n_held, const int *held, const float *src, int src_on_device, void *stream,
+                                 vr_volume *out);
 vr_status vr_volume_release(vr_volume vol);
 /* Number of bricks, their voxel boxes (n x 6 ints, may be NULL) and the bytes
  * of brick storage in device memory (may be NULL). */
@@ -252,6 +263,15 @@ vr_status vr_frame_partial(vr_frame fr, int brick, const float **dev_ptr);
  * host output makes the call synchronous). */
 vr_status vr_composite(vr_ctx ctx, vr_frame fr, float *out_rgba, int out_on_device, void *stream);
 vr_status vr_frame_release(vr_frame fr);
+/* Sec. 3: the ranks' images end up composited into one framebuffer. out_dev =
+ * images_dev[0] over images_dev[1] over ... over images_dev[n-1], pixel by pixel
+ * (front to back; premultiplied RGBA, "over" as above), for `pixels` pixels of
+ * float32 RGBA in device memory (1 <= n <= VR_MAX_BRICKS; every pointer 16-byte
+ * aligned, else VR_ERR_ARG). `images_dev` is a host array of device pointers.
+ * out_dev may be images_dev[0]. This is the combining step of each round of a
+ * radix-k image exchange between GPUs (paper_2501_01628_gb300/sharded.py). */
+vr_status vr_composite_images(vr_ctx ctx, int n, const float *const *images_dev, float *out_dev, long long pixels,
+                              void *stream);
 /* Steps 1 + 2 with a context-owned frame (no allocation once warm). */
 vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on_device,
                           void *stream);

@@ -503,6 +503,7 @@ vr_status vr_batch_create(vr_ctx ctx, int n_volumes, const vr_volume *vols, cons
         if (!v || v->ctx != ctx) return fail(ctx, VR_ERR_ARG, "volume missing or from another context");
         if (std::memcmp(v->dims, v0->dims, sizeof(v0->dims)) != 0 || v->boxes != v0->boxes || v->dtype != v0->dtype)
             return fail(ctx, VR_ERR_ARG, "batched volumes must share dims, partition and storage type");
+        if (!v->held.empty()) return fail(ctx, VR_ERR_ARG, "batched volumes must hold every brick (no shares)");
     }
     for (int w = 0; w < n_views; ++w) {
         const vr_camera &c = cams[w];

@@ -341,7 +341,7 @@ cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
         const int *bx = &vol->boxes[6 * b];
         PackBrick &B = pp.b[b];
         B.dst = static_cast<char *>(vol->d_data) + vol->base[b] * static_cast<long long>(es);
-        B.quads = brick_quads(bx);
+        B.quads = vol->holds(b) ? brick_quads(bx) : 0;
         for (int a = 0; a < 3; ++a) {
             B.lo[a] = bx[a];
             B.s[a] = bx[3 + a] - bx[a] + 2;
@@ -361,7 +361,7 @@ cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
         PackBrick &B = pp.b[b];
         B.dst = vol->d_scalar + vol->sbase[b];
         B.row = vol->sxp[b];
-        B.quads = static_cast<long long>(B.row) * B.s[1] * B.s[2];
+        B.quads = vol->holds(b) ? static_cast<long long>(B.row) * B.s[1] * B.s[2] : 0;
         B.block_begin = static_cast<int>(blocks);
         blocks += (B.quads + kPackChunk - 1) / kPackChunk;
     }
@@ -411,6 +411,7 @@ vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &
     for (int b = 0; b < nb; ++b) {
         int *r = &fr.rects[4 * b];
         footprint(c, B, &vol->boxes[6 * b], nmax, r);
+        if (!vol->holds(b)) r[0] = r[1] = r[2] = r[3] = 0;  // not in this share: an empty partial
         fr.poff[b] = px;
         px += static_cast<long long>(r[2]) * r[3];
         px = (px + 7) & ~7LL;  // 128-byte aligned partial starts
@@ -841,10 +842,10 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
     return VR_OK;
 }
 
-vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, const vr_partition *part,
-                           const float *src, int src_on_device, void *stream, vr_volume *out)
+namespace {
+vr_status create_volume(vr_ctx ctx, const int dims[3], vr_dtype storage, const vr_partition *part, int n_held,
+                        const int *held, const float *src, int src_on_device, void *stream, vr_volume *out)
 {
-    vr::host::TraceRange trace_("vr_volume_create");
     if (!ctx || !out) return VR_ERR_ARG;
     *out = nullptr;
     if (!dims || !part || !src) return fail(ctx, VR_ERR_ARG, "null argument");
@@ -862,16 +863,27 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
     for (int b = 0; b < nb; ++b)
         if (brick_quads(&vol->boxes[6 * b]) > 0x7fffffffLL)
             return fail(ctx, VR_ERR_ARG, "a brick holds more than 2^31 - 1 quads (about 1290^3 voxels); use more bricks");
+    if (held) {
+        if (n_held < 1 || n_held > nb) return fail(ctx, VR_ERR_ARG, "a share holds 1 to n_bricks bricks");
+        vol->held.assign(nb, 0);
+        for (int i = 0; i < n_held; ++i) {
+            if (held[i] < 0 || held[i] >= nb || vol->held[held[i]])
+                return fail(ctx, VR_ERR_ARG, "share brick ids must be distinct brick ids of the partition");
+            vol->held[held[i]] = 1;
+        }
+    }
 
-    // brick-major haloed xy-quad storage, each brick 256-byte aligned
+    // brick-major haloed xy-quad storage of the held bricks, each 256-byte aligned
     const size_t es = quad_size(storage);
     long long off_bytes = 0;
     vol->base.resize(nb);
     for (int b = 0; b < nb; ++b) {
         vol->base[b] = off_bytes / static_cast<long long>(es);
+        if (!vol->holds(b)) continue;
         off_bytes += brick_quads(&vol->boxes[6 * b]) * static_cast<long long>(es);
         off_bytes = (off_bytes + 255) & ~255LL;
     }
+    off_bytes = std::max(off_bytes, 256LL);
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VR_CUDA(ctx, vr::host::dev_malloc(&vol->d_data, static_cast<size_t>(off_bytes)));
@@ -886,9 +898,11 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
             const int *bx = &vol->boxes[6 * b];
             vol->sxp[b] = (bx[3] - bx[0] + 2 + 3) & ~3;
             vol->sbase[b] = off;
+            if (!vol->holds(b)) continue;
             off += static_cast<long long>(vol->sxp[b]) * (bx[4] - bx[1] + 2) * (bx[5] - bx[2] + 2);
             off = (off + 31) & ~31LL;
         }
+        off = std::max(off, 32LL);
         const cudaError_t es2 = vr::host::dev_malloc(&vol->d_scalar, static_cast<size_t>(off) * sizeof(float));
         if (es2 != cudaSuccess) {
             cudaFree(vol->d_data);
@@ -921,6 +935,23 @@ vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, cons
     ctx->live_objects++;
     *out = vol.release();
     return VR_OK;
+}
+}  // namespace
+
+vr_status vr_volume_create(vr_ctx ctx, const int dims[3], vr_dtype storage, const vr_partition *part,
+                           const float *src, int src_on_device, void *stream, vr_volume *out)
+{
+    vr::host::TraceRange trace_("vr_volume_create");
+    return create_volume(ctx, dims, storage, part, 0, nullptr, src, src_on_device, stream, out);
+}
+
+vr_status vr_volume_create_share(vr_ctx ctx, const int dims[3], vr_dtype storage, const vr_partition *part,
+                                 int n_held, const int *held, const float *src, int src_on_device, void *stream,
+                                 vr_volume *out)
+{
+    vr::host::TraceRange trace_("vr_volume_create_share");
+    if (!held) return ctx ? fail(ctx, VR_ERR_ARG, "null share") : VR_ERR_ARG;
+    return create_volume(ctx, dims, storage, part, n_held, held, src, src_on_device, stream, out);
 }
 
 vr_status vr_volume_update(vr_volume vol, const float *src, int src_on_device, void *stream)
@@ -1045,6 +1076,7 @@ vr_status vr_volume_read_brick(vr_volume vol, int brick, void *dst, size_t bytes
     if (!vol || !dst) return VR_ERR_ARG;
     const int nb = static_cast<int>(vol->boxes.size() / 6);
     if (brick < 0 || brick >= nb) return fail(vol->ctx, VR_ERR_ARG, "brick index out of range");
+    if (!vol->holds(brick)) return fail(vol->ctx, VR_ERR_ARG, "the brick is not in this volume's share");
     const int *bx = &vol->boxes[6 * brick];
     const int sx = bx[3] - bx[0] + 2, sy = bx[4] - bx[1] + 2, sz = bx[5] - bx[2] + 2;
     const size_t es = elem_size(vol->dtype);
@@ -1234,6 +1266,28 @@ vr_status vr_set_host_output_async(vr_ctx ctx, int on)
 {
     if (!ctx) return VR_ERR_ARG;
     ctx->host_async = on != 0;
+    return VR_OK;
+}
+
+vr_status vr_composite_images(vr_ctx ctx, int n, const float *const *images_dev, float *out_dev, long long pixels,
+                              void *stream)
+{
+    vr::host::TraceRange trace_("vr_composite_images");
+    if (!ctx) return VR_ERR_ARG;
+    if (n < 1 || n > kMaxBricks || !images_dev || !out_dev || pixels < 0)
+        return fail(ctx, VR_ERR_ARG, "1 to VR_MAX_BRICKS images, an output and a pixel count >= 0");
+    static thread_local ImagesParams ip;
+    for (int j = 0; j < n; ++j) {
+        if (!images_dev[j] || (reinterpret_cast<uintptr_t>(images_dev[j]) & 15))
+            return fail(ctx, VR_ERR_ARG, "image pointers must be non-null and 16-byte aligned");
+        ip.img[j] = reinterpret_cast<const float4 *>(images_dev[j]);
+    }
+    if (reinterpret_cast<uintptr_t>(out_dev) & 15) return fail(ctx, VR_ERR_ARG, "output must be 16-byte aligned");
+    ip.n = n;
+    ip.pixels = pixels;
+    ip.out = reinterpret_cast<float4 *>(out_dev);
+    DeviceGuard g(ctx->device);
+    VR_LAUNCH(ctx, launch_composite_images(ip, static_cast<cudaStream_t>(stream)));
     return VR_OK;
 }
 

@@ -174,6 +174,14 @@ struct BatchParams {
     int wait_extra;                  // added to unit 0's march target by composite waits (test hook; 0)
 };
 
+// "over" of n images, front to back, pixel by pixel (vr_composite_images).
+struct ImagesParams {
+    const float4 *img[kMaxBricks];
+    int n;
+    long long pixels;
+    float4 *out;
+};
+
 // Pack of all bricks of a volume in one launch: block j of brick b (counted
 // from that brick's block_begin) writes the brick's storage quads
 // [j*kPackChunk, (j+1)*kPackChunk), in storage order.
@@ -209,6 +217,7 @@ cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s);
 cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s);
 cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out, cudaStream_t s);
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s);
+cudaError_t launch_composite_images(const ImagesParams &p, cudaStream_t s);
 // Tile masks of p (p.tile_mask) for frames whose march did not write them.
 cudaError_t launch_tile_masks(const CompositeParams &p, cudaStream_t s);
 cudaError_t launch_composite_grad(const CompositeGradParams &p, cudaStream_t s);

@@ -5,6 +5,8 @@
 // renders its share. Sec. 3/4: the per-rank images are composited into one
 // framebuffer. The optical model is the standard emission-absorption one; the
 // exact per-sample definitions are stated in include/vr.h.
+#include <algorithm>
+
 #include "vr_device.cuh"
 
 namespace vr {
@@ -255,6 +257,22 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Images of ranks (shares of the bricks) composited front to back: the step of
+// each radix-k exchange round between GPUs (Sec. 3: the ranks' images end up
+// composited in one framebuffer). Grid-stride over pixels; every input pixel is
+// read once, so a pixel's output may overwrite its first input.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) composite_images_kernel(const __grid_constant__ ImagesParams p)
+{
+    const long long stride = static_cast<long long>(gridDim.x) * 256;
+    for (long long i = static_cast<long long>(blockIdx.x) * 256 + threadIdx.x; i < p.pixels; i += stride) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < p.n; ++j) acc = over(acc, __ldcs(p.img[j] + i));
+        __stcs(p.out + i, acc);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -311,6 +329,18 @@ cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out
     default: return cudaErrorInvalidValue;
     }
 #undef VR_CYCLE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_images(const ImagesParams &p, cudaStream_t s)
+{
+    if (p.pixels <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long blocks = std::min<long long>((p.pixels + 255) / 256, static_cast<long long>(sms) * 8);
+    composite_images_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

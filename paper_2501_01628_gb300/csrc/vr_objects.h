@@ -136,6 +136,11 @@ struct vr_volume_s {
     float *d_scalar = nullptr;
     std::vector<long long> sbase;
     std::vector<int> sxp;
+    // a rank's share (vr_volume_create_share): held[b] != 0 for the bricks this
+    // volume stores; empty = every brick. Bricks not held have no storage and
+    // render as empty partials (the identity of "over").
+    std::vector<char> held;
+    bool holds(int b) const { return held.empty() || held[b]; }
 };
 
 namespace vr {

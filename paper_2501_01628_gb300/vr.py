@@ -40,6 +40,7 @@ EXPORTS = (
     "vr_set_opacity_correction", "vr_volume_update_async", "vr_set_packet_width",
     "vr_set_host_output_async", "vr_mesh_create", "vr_mesh_release", "vr_mesh_info",
     "vr_render_mesh_frame", "vr_debug_inject_fault", "vr_batch_debug_wait", "vr_set_march_staging",
+    "vr_volume_create_share", "vr_composite_images",
 )
 
 
@@ -71,6 +72,9 @@ _SIG = {
     "vr_sync": (_I, [_P, _P]),
     "vr_volume_create": (_I, [_P, _P, _I, ctypes.POINTER(vr_partition), _P, _I, _P, ctypes.POINTER(_P)]),
     "vr_volume_release": (_I, [_P]),
+    "vr_volume_create_share": (_I, [_P, _P, _I, ctypes.POINTER(vr_partition), _I, _P, _P, _I, _P,
+                                    ctypes.POINTER(_P)]),
+    "vr_composite_images": (_I, [_P, _I, _P, _P, ctypes.c_longlong, _P]),
     "vr_volume_info": (_I, [_P, _P, _P, _P]),
     "vr_volume_read_brick": (_I, [_P, _I, _P, ctypes.c_size_t]),
     "vr_set_transfer_function": (_I, [_P, _P, _I, ctypes.c_float, ctypes.c_float, _I]),
@@ -300,6 +304,38 @@ def vr_volume_create(ctx, volume, storage: str = "f32", partition=None, stream=N
                                   _stream(stream), ctypes.byref(h)), ctx, "vr_volume_create")
     _vol_shape[_key(h)] = (nz, ny, nx)
     return h
+
+
+def vr_volume_create_share(ctx, volume, held, storage: str = "f32", partition=None, stream=None):
+    """A rank's share: only the bricks in `held` (brick ids of the partition)
+    are stored and marched; the others render as empty partials."""
+    ptr, on_dev, keep = _array(volume, "volume", ndim=3)
+    nz, ny, nx = tuple(keep.shape)
+    dims = (ctypes.c_int * 3)(nx, ny, nz)
+    part, pk = make_partition(**(partition or {}))
+    ids = np.ascontiguousarray(list(held), dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().vr_volume_create_share(ctx, dims, DTYPES[storage], ctypes.byref(part), int(ids.size),
+                                        ids.ctypes.data, ptr, on_dev, _stream(stream), ctypes.byref(h)), ctx,
+           "vr_volume_create_share")
+    _vol_shape[_key(h)] = (nz, ny, nx)
+    return h
+
+
+def vr_composite_images(ctx, images, out, stream=None):
+    """out = images[0] over images[1] over ... (front to back), pixel by pixel;
+    CUDA float32 tensors of one shape [..., 4]. out may be images[0]."""
+    if not images:
+        raise ValueError("at least one image")
+    shape = tuple(images[0].shape)
+    if len(shape) < 1 or shape[-1] != 4:
+        raise ValueError("images are [..., 4] RGBA")
+    ptrs = [_array(im, "image", shape=shape, device=True)[0] for im in images]
+    optr, _, _ = _array(out, "out", shape=shape, device=True, writable=True)
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    pixels = int(np.prod(shape[:-1]))
+    _check(lib().vr_composite_images(ctx, len(ptrs), arr, optr, pixels, _stream(stream)), ctx,
+           "vr_composite_images")
 
 
 def vr_batch_create(ctx, vols, cams, out, vmins=None, vmaxs=None):
