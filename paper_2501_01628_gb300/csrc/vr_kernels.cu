@@ -223,12 +223,14 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
                 if (pos[u] >= 0) {
                     if (LEVELS > 1 && prev >= 0) {
                         const int c = carried_levels(p, prev, pos[u]);
+                        if (c > 0) {  // uniform: most listed bricks close no group
 #pragma unroll
-                        for (int l = 0; l + 1 < LEVELS; ++l)
-                            if (l < c) {
-                                acc[l + 1] = over(acc[l + 1], acc[l]);
-                                acc[l] = zero;
-                            }
+                            for (int l = 0; l + 1 < LEVELS; ++l)
+                                if (l < c) {
+                                    acc[l + 1] = over(acc[l + 1], acc[l]);
+                                    acc[l] = zero;
+                                }
+                        }
                     }
                     acc[0] = over(acc[0], v[u]);
                     prev = pos[u];
