@@ -38,9 +38,10 @@ UNIT = "samples/s"
 # test 1).
 FLOPS_PER_SAMPLE = 66
 FP32_LANES = 128  # FP32 lanes per SM (sm_100 family)
-# kernel durations are taken from event pairs around the launches of every
-# KT_STRIDE-th timed frame (7 is coprime with the 8 orbit views)
-KT_STRIDE = 7
+# kernel durations come from a separate pass after the timed region, with event
+# pairs around every march and composite launch (they cost about 10 us per
+# frame, so the timed region itself carries none): at least KT_FRAMES frames
+KT_FRAMES = 64
 
 
 def args_parse():
@@ -159,7 +160,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -370,10 +371,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i, vi in enumerate(timed_views):
-        # per-kernel event pairs on every KT_STRIDE-th frame only (they cost
-        # about 10 us per frame); the stride is coprime with the 8 orbit views
-        vr.vr_set_kernel_timing(ctx, i % KT_STRIDE == 0)
+    for vi in timed_views:
         vr.vr_set_camera(ctx, cams[vi])
         vr.vr_render_frame(ctx, v, out)
     e1.record(stream)
@@ -381,6 +379,13 @@ def run_ours(a):
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+
+    # ---- per-kernel durations: a separate pass with event pairs on every launch
+    vr.vr_set_kernel_timing(ctx, True)
+    kt_frames = max(KT_FRAMES, len(timed_views))
+    for i in range(kt_frames):  # the orbit views in turn
+        vr.vr_set_camera(ctx, cams[i % len(cams)])
+        vr.vr_render_frame(ctx, v, out)
     kt = vr.vr_get_kernel_timing(ctx)
     vr.vr_set_kernel_timing(ctx, False)
 
@@ -932,14 +937,17 @@ def run_mesh(a):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i, vi in enumerate(timed_views):
-        vr.vr_set_kernel_timing(ctx, i % KT_STRIDE == 0)
+    for vi in timed_views:
         vr.vr_set_camera(ctx, cams[vi])
         vr.vr_render_mesh_frame(ctx, m, out)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    vr.vr_set_kernel_timing(ctx, True)  # per-kernel durations: a separate pass
+    for i in range(max(KT_FRAMES // 4, len(timed_views))):
+        vr.vr_set_camera(ctx, cams[i % len(cams)])
+        vr.vr_render_mesh_frame(ctx, m, out)
     kt = vr.vr_get_kernel_timing(ctx)
     vr.vr_set_kernel_timing(ctx, False)
     hosts = [torch.empty((H, W, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
