@@ -20,9 +20,9 @@
 // even one sample's box fits, the block samples that slab straight from the
 // scalar brick in global memory.
 //
-// Every wait is bounded: a wait that gives up sets bit 32 of the device error
-// word (vr_sync reports VR_ERR_TIMEOUT), and the block stops after waiting,
-// again bounded, for its copies in flight.
+// Every wait is bounded: a wait that gives up sets bit 5 (value 32) of the
+// device error word (vr_sync reports VR_ERR_TIMEOUT), and the block stops after
+// waiting, again bounded, for its copies in flight.
 #include "vr_device.cuh"
 
 namespace vr {
