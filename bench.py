@@ -439,6 +439,27 @@ def run_ours(a):
                                note="bfloat16 brick storage (8-byte quads), FP32 accumulation; accuracy against "
                                     "the FP64 oracle is checked on the 1024^3 precision workload"))
         vr.vr_volume_release(vb)
+        # the same with the octet cell layout (both planes of a cell per 16-byte
+        # element: one load per sample; the image is bit-identical to the quads')
+        vr.vr_set_cell_layout(ctx, 1)
+        vo = vr.vr_volume_create(ctx, vol, "bf16", wl["part"])
+        vr.vr_set_cell_layout(ctx, 0)
+        for i in range(a.warmup):
+            vr.vr_set_camera(ctx, cams[views[i]])
+            vr.vr_render_frame(ctx, vo, out)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for vi in timed_views[:nb16]:
+            vr.vr_set_camera(ctx, cams[vi])
+            vr.vr_render_frame(ctx, vo, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        oms = e0.elapsed_time(e1) / nb16
+        forms["bf16_octets"] = dict(ms_per_frame=oms, frames=nb16, speedup_vs_f32=fms / oms,
+                                    samples_per_s=sum(counts[vi] for vi in timed_views[:nb16]) / (oms * nb16 / 1e3),
+                                    note="bfloat16 storage as octets (vr_set_cell_layout 1): one 16-byte load per "
+                                         "sample, storage as large as float32 xy-quads")
+        vr.vr_volume_release(vo)
 
     # ray-state cycling on the same frames (rays carry (C, T) through the bricks,
     # global early termination): executed samples and frame time

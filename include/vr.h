@@ -214,6 +214,15 @@ vr_status vr_set_packet_width(vr_ctx ctx, int packet_width);
  * Each bounded wait for a staged slab that gives up makes the next vr_sync
  * return VR_ERR_TIMEOUT. */
 vr_status vr_set_march_staging(vr_ctx ctx, int on);
+/* Cell layout of bfloat16 / float16 volumes created afterwards (the precision
+ * form: 16-bit storage, float32 arithmetic). 0 (default): xy-quads, four
+ * voxels of one plane per 8-byte element, two loads per sample. 1: octets,
+ * both planes of a cell in one 16-byte element, one load per sample: twice the
+ * memory of xy-quads (as much as float32 xy-quads), faster where the march is
+ * bound by its loads. The image is the same bit for bit. Float32 volumes
+ * always use xy-quads (float32 octets measured slower). Volumes of one batch
+ * must share the layout. VR_ERR_ARG for another value. */
+vr_status vr_set_cell_layout(vr_ctx ctx, int layout);
 /* Frame algorithm of vr_render_frame.
  *   0 (default): sort-last -- one partial image per brick, then the "over"
  *     composite (the steps above).

@@ -211,26 +211,38 @@ cudaError_t launch_batch_t(const BatchParams &p, int blocks, cudaStream_t s)
 
 }  // namespace
 
-cudaError_t launch_batch(const BatchParams &p, vr_dtype dtype, int blocks, cudaStream_t s)
+template <typename S>
+cudaError_t launch_batch_s(const BatchParams &p, int blocks, cudaStream_t s)
 {
-    const bool opc = p.opc_ratio != 1.0f;
-    switch (dtype) {
-    case VR_F32: return opc ? launch_batch_t<float, true>(p, blocks, s) : launch_batch_t<float, false>(p, blocks, s);
-    case VR_BF16:
-        return opc ? launch_batch_t<__nv_bfloat16, true>(p, blocks, s) : launch_batch_t<__nv_bfloat16, false>(p, blocks, s);
-    case VR_F16: return opc ? launch_batch_t<__half, true>(p, blocks, s) : launch_batch_t<__half, false>(p, blocks, s);
+    return p.opc_ratio != 1.0f ? launch_batch_t<S, true>(p, blocks, s) : launch_batch_t<S, false>(p, blocks, s);
+}
+
+cudaError_t launch_batch(const BatchParams &p, int kind, int blocks, cudaStream_t s)
+{
+    switch (kind) {
+    case kStoreF32: return launch_batch_s<float>(p, blocks, s);
+    case kStoreBF16: return launch_batch_s<__nv_bfloat16>(p, blocks, s);
+    case kStoreF16: return launch_batch_s<__half>(p, blocks, s);
+    case kStoreBF16Oct: return launch_batch_s<dev::Octet<__nv_bfloat16>>(p, blocks, s);
+    case kStoreF16Oct: return launch_batch_s<dev::Octet<__half>>(p, blocks, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-int batch_max_blocks_per_sm(vr_dtype dtype)
+int batch_max_blocks_per_sm(int kind)
 {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    switch (dtype) {
-    case VR_F32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<float, true>, 128, 0); break;
-    case VR_BF16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<__nv_bfloat16, true>, 128, 0); break;
-    case VR_F16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<__half, true>, 128, 0); break;
+    switch (kind) {
+    case kStoreF32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<float, true>, 128, 0); break;
+    case kStoreBF16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<__nv_bfloat16, true>, 128, 0); break;
+    case kStoreF16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<__half, true>, 128, 0); break;
+    case kStoreBF16Oct:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<dev::Octet<__nv_bfloat16>, true>, 128, 0);
+        break;
+    case kStoreF16Oct:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<dev::Octet<__half>, true>, 128, 0);
+        break;
     default: break;
     }
     return e == cudaSuccess ? n : 0;
@@ -252,6 +264,7 @@ struct vr_batch_s {
     float *out = nullptr;
     int nb = 0, W = 0, H = 0;
     vr_dtype dtype = VR_F32;
+    int kind = kStoreF32;  // storage type and cell layout (StorageKind)
     int pw = 8, bps = 0, slots = 16, mode = 0;
     // device tables
     BatchView *d_views = nullptr;
@@ -427,7 +440,7 @@ vr_status build(vr_batch b, int pw, int bps, int mode)
     }
     int sms = 0;
     VR_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    const int maxb = batch_max_blocks_per_sm(b->dtype);
+    const int maxb = batch_max_blocks_per_sm(b->kind);
     if (maxb < 1) return fail(ctx, VR_ERR_CUDA, "batched kernel cannot be resident");
     bps = std::max(1, std::min(bps > 0 ? bps : maxb, maxb));
     b->pw = pw;
@@ -472,7 +485,7 @@ vr_status build(vr_batch b, int pw, int bps, int mode)
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_march_done, 0, nu * sizeof(int), b->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_comp_done, 0, nu * sizeof(int), b->cap);
     if (e == cudaSuccess && vr::host::fault_now(VR_FAULT_LAUNCH)) e = cudaErrorLaunchFailure;
-    if (e == cudaSuccess) e = launch_batch(p, b->dtype, sms * bps, b->cap);
+    if (e == cudaSuccess) e = launch_batch(p, b->kind, sms * bps, b->cap);
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -504,6 +517,7 @@ vr_status vr_batch_create(vr_ctx ctx, int n_volumes, const vr_volume *vols, cons
         if (std::memcmp(v->dims, v0->dims, sizeof(v0->dims)) != 0 || v->boxes != v0->boxes || v->dtype != v0->dtype)
             return fail(ctx, VR_ERR_ARG, "batched volumes must share dims, partition and storage type");
         if (!v->held.empty()) return fail(ctx, VR_ERR_ARG, "batched volumes must hold every brick (no shares)");
+        if (v->octets != v0->octets) return fail(ctx, VR_ERR_ARG, "batched volumes must share the cell layout");
     }
     for (int w = 0; w < n_views; ++w) {
         const vr_camera &c = cams[w];
@@ -522,6 +536,7 @@ vr_status vr_batch_create(vr_ctx ctx, int n_volumes, const vr_volume *vols, cons
     b->W = cams[0].width;
     b->H = cams[0].height;
     b->dtype = v0->dtype;
+    b->kind = storage_kind(v0->dtype, v0->octets);
     for (int i = 0; i < n_volumes; ++i) {
         const double lo = vmins ? vmins[i] : ctx->vmin, hi = vmaxs ? vmaxs[i] : ctx->vmax;
         if (!(hi > lo)) return fail(ctx, VR_ERR_ARG, "batched volume range must have vmax > vmin");
@@ -574,7 +589,7 @@ vr_status vr_batch_autotune(vr_batch b, void *stream, const char *cache_path, in
     char key[512];
     std::snprintf(key, sizeof(key), "%s|v%zu|w%zu|b%d|%dx%d|%dx%dx%d|t%d", prop.name, b->vols.size(), b->cams.size(),
                   b->nb, b->W, b->H, b->vols[0]->dims[0], b->vols[0]->dims[1], b->vols[0]->dims[2],
-                  static_cast<int>(b->dtype));
+                  b->kind);
     int best_pw = 0, best_bps = 0, best_mode = 0;
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "r")) {
@@ -594,7 +609,7 @@ vr_status vr_batch_autotune(vr_batch b, void *stream, const char *cache_path, in
     }
     float best_ms = 0.0f;
     if (!best_pw) {
-        const int maxb = batch_max_blocks_per_sm(b->dtype);
+        const int maxb = batch_max_blocks_per_sm(b->kind);
         const int pws[3] = {4, 8, 16};
         std::vector<int> bpss;
         for (int c : {maxb / 2, (3 * maxb) / 4, maxb})

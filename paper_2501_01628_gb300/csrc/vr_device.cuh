@@ -20,6 +20,7 @@ namespace dev {
 // ---------------------------------------------------------------------------
 template <typename T> struct Quad;
 template <> struct Quad<float> {
+    static constexpr bool octet = false;
     using type = float4;
     static __device__ __forceinline__ float4 load(const float4 *p) { return __ldg(p); }
     static __device__ __forceinline__ float4 make(float a, float b, float c, float d)
@@ -28,13 +29,14 @@ template <> struct Quad<float> {
     }
 };
 template <> struct Quad<__nv_bfloat16> {
+    static constexpr bool octet = false;
     using type = uint2;
-    static __device__ __forceinline__ float4 load(const uint2 *p)
+    static __device__ __forceinline__ float4 load_bits(uint2 u)
     {
-        const uint2 u = __ldg(p);
         return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
                            __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
     }
+    static __device__ __forceinline__ float4 load(const uint2 *p) { return load_bits(__ldg(p)); }
     static __device__ __forceinline__ uint2 make(float a, float b, float c, float d)
     {
         auto bits = [](float v) {
@@ -44,20 +46,45 @@ template <> struct Quad<__nv_bfloat16> {
     }
 };
 template <> struct Quad<__half> {
+    static constexpr bool octet = false;
     using type = uint2;
-    static __device__ __forceinline__ float4 load(const uint2 *p)
+    static __device__ __forceinline__ float4 load_bits(uint2 u)
     {
-        const uint2 u = __ldg(p);
         const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
         const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
         return make_float4(lo.x, lo.y, hi.x, hi.y);
     }
+    static __device__ __forceinline__ float4 load(const uint2 *p) { return load_bits(__ldg(p)); }
     static __device__ __forceinline__ uint2 make(float a, float b, float c, float d)
     {
         auto bits = [](float v) { return static_cast<unsigned>(__half_as_ushort(__float2half_rn(v))); };
         return make_uint2(bits(a) | (bits(b) << 16), bits(c) | (bits(d) << 16));
     }
 };
+
+// "Octets": 16-bit storage with both planes of a cell in one 16-byte element,
+// (plane k quad, plane k+1 quad), at the quad's index. A sample is then one
+// 128-bit load; the storage is twice that of 16-bit xy-quads (the same as
+// float32 xy-quads). Octet<T> tags the layout in the kernels' templates.
+template <typename T> struct Octet {};
+template <typename T> struct OctetOf {
+    static constexpr bool octet = true;
+    using type = uint4;
+    static __device__ __forceinline__ void load2(const uint4 *p, float4 &a0, float4 &a1)
+    {
+        const uint4 u = __ldg(p);
+        a0 = Quad<T>::load_bits(make_uint2(u.x, u.y));
+        a1 = Quad<T>::load_bits(make_uint2(u.z, u.w));
+    }
+    static __device__ __forceinline__ uint4 make8(float a, float b, float c, float d, float e, float f, float g,
+                                                  float h)
+    {
+        const uint2 lo = Quad<T>::make(a, b, c, d), hi = Quad<T>::make(e, f, g, h);
+        return make_uint4(lo.x, lo.y, hi.x, hi.y);
+    }
+};
+template <> struct Quad<Octet<__nv_bfloat16>> : OctetOf<__nv_bfloat16> {};
+template <> struct Quad<Octet<__half>> : OctetOf<__half> {};
 
 __device__ __forceinline__ int find_brick(const MarchParams &p, int item)
 {
@@ -338,14 +365,23 @@ __device__ __forceinline__ void march_accumulate(const void *data, const BrickLa
         unsigned ca, ca1, cb, cb1;
         cells(__float_as_uint(fxa), __float_as_uint(fya), __float_as_uint(fza), ca, ca1, true);
         cells(__float_as_uint(fxb), __float_as_uint(fyb), __float_as_uint(fzb), cb, cb1, two);
-        if (ca != prev) {
-            q0 = Quad<S>::load(vox + ca);
-            q1 = Quad<S>::load(vox + ca1);
-        }
-        float4 r0 = q0, r1 = q1;
-        if (two && cb != ca) {
-            r0 = Quad<S>::load(vox + cb);
-            r1 = Quad<S>::load(vox + cb1);
+        float4 r0, r1;
+        if constexpr (Quad<S>::octet) {  // both planes in one element
+            if (ca != prev) Quad<S>::load2(vox + ca, q0, q1);
+            r0 = q0;
+            r1 = q1;
+            if (two && cb != ca) Quad<S>::load2(vox + cb, r0, r1);
+        } else {
+            if (ca != prev) {
+                q0 = Quad<S>::load(vox + ca);
+                q1 = Quad<S>::load(vox + ca1);
+            }
+            r0 = q0;
+            r1 = q1;
+            if (two && cb != ca) {
+                r0 = Quad<S>::load(vox + cb);
+                r1 = Quad<S>::load(vox + cb1);
+            }
         }
         // both samples' table coordinates x = clamp((s - vmin)/(vmax - vmin), 0, 1)(n - 1)
         const float sa = trilinear(q0, q1, ax, ay_, az_);

@@ -142,8 +142,13 @@ __global__ void __launch_bounds__(128) march_grad_kernel(const __grid_constant__
             q.i = min(max(static_cast<int>(flx), 0), imax);
             q.j = min(max(static_cast<int>(fly), 0), jmax);
             q.k = min(max(static_cast<int>(flz), 0), kmax);
-            const float4 a0 = Quad<S>::load(vox + quad_index(q.i, q.j, q.k, nbx, nby));
-            const float4 a1 = Quad<S>::load(vox + quad_index(q.i, q.j, q.k + 1, nbx, nby));
+            float4 a0, a1;
+            if constexpr (Quad<S>::octet) {
+                Quad<S>::load2(vox + quad_index(q.i, q.j, q.k, nbx, nby), a0, a1);
+            } else {
+                a0 = Quad<S>::load(vox + quad_index(q.i, q.j, q.k, nbx, nby));
+                a1 = Quad<S>::load(vox + quad_index(q.i, q.j, q.k + 1, nbx, nby));
+            }
             const float c00 = fmaf(q.wx, a0.y - a0.x, a0.x), c10 = fmaf(q.wx, a0.w - a0.z, a0.z);
             const float c01 = fmaf(q.wx, a1.y - a1.x, a1.x), c11 = fmaf(q.wx, a1.w - a1.z, a1.z);
             const float c0 = fmaf(q.wy, c10 - c00, c00), c1 = fmaf(q.wy, c11 - c01, c01);
@@ -278,14 +283,16 @@ cudaError_t launch_composite_grad(const CompositeGradParams &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, vr_dtype dtype, cudaStream_t s)
+cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, int kind, cudaStream_t s)
 {
     if (p.n_items <= 0) return cudaSuccess;
     const size_t smem = 4 * static_cast<size_t>(p.ntf) * sizeof(float);
-    switch (dtype) {
-    case VR_F32: march_grad_kernel<float><<<p.n_items, 128, smem, s>>>(p, g); break;
-    case VR_BF16: march_grad_kernel<__nv_bfloat16><<<p.n_items, 128, smem, s>>>(p, g); break;
-    case VR_F16: march_grad_kernel<__half><<<p.n_items, 128, smem, s>>>(p, g); break;
+    switch (kind) {
+    case kStoreF32: march_grad_kernel<float><<<p.n_items, 128, smem, s>>>(p, g); break;
+    case kStoreBF16: march_grad_kernel<__nv_bfloat16><<<p.n_items, 128, smem, s>>>(p, g); break;
+    case kStoreF16: march_grad_kernel<__half><<<p.n_items, 128, smem, s>>>(p, g); break;
+    case kStoreBF16Oct: march_grad_kernel<dev::Octet<__nv_bfloat16>><<<p.n_items, 128, smem, s>>>(p, g); break;
+    case kStoreF16Oct: march_grad_kernel<dev::Octet<__half>><<<p.n_items, 128, smem, s>>>(p, g); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

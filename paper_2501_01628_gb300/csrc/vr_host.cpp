@@ -38,7 +38,9 @@ bool fault_now(int kind)
 
 size_t elem_size(vr_dtype t) { return t == VR_F32 ? 4 : 2; }
 // bytes of one xy-quad (four voxels) in device storage
-size_t quad_size(vr_dtype t) { return 4 * elem_size(t); }
+// bytes of one storage element: an xy-quad (four voxels), or an octet (both
+// planes of a cell, 16-bit types only)
+size_t quad_size(vr_dtype t, bool octets) { return (octets && t != VR_F32 ? 8 : 4) * elem_size(t); }
 // quads stored for a brick: haloed extents (sx, sy, sz) give (sx-1) x (sy-1) x sz
 // quads, rounded up to whole 2x2x2 blocks
 long long brick_quads(const int *bx)
@@ -330,7 +332,7 @@ bool camera_valid(const vr_camera *cam)
 // Pack every brick of `vol` from the device float32 volume `dsrc`.
 cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
 {
-    const size_t es = quad_size(vol->dtype);
+    const size_t es = quad_size(vol->dtype, vol->octets);
     const int nb = static_cast<int>(vol->boxes.size() / 6);
     static thread_local PackParams pp;
     pp.src = dsrc;
@@ -353,7 +355,7 @@ cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     pp.n_blocks = static_cast<int>(blocks);
     if (fault_now(VR_FAULT_LAUNCH)) return cudaErrorLaunchFailure;
-    cudaError_t e = launch_pack(pp, vol->dtype, s);
+    cudaError_t e = launch_pack(pp, vol->kind(), s);
     if (e != cudaSuccess || !vol->d_scalar) return e;
     // the staged march's scalar copy
     blocks = 0;
@@ -530,7 +532,7 @@ vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s)
         }
         VR_LAUNCH(ctx, launch_march_staged(mp, sb, s));
     } else {
-        VR_LAUNCH(ctx, launch_march(mp, vol->dtype, s));
+        VR_LAUNCH(ctx, launch_march(mp, vol->kind(), s));
     }
     timing_end(ctx, t, s);
     fr.masks_ready = true;
@@ -671,7 +673,7 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
         if (st != VR_OK) return st;
     }
     const int t = timing_begin(ctx, 0, s);
-    VR_LAUNCH(ctx, launch_march_cycle(mp, vol->dtype, dst, s));
+    VR_LAUNCH(ctx, launch_march_cycle(mp, vol->kind(), dst, s));
     timing_end(ctx, t, s);
     if (!out_on_device) return host_copy(ctx, out, dst, slot, px, s);
     return VR_OK;
@@ -856,6 +858,7 @@ vr_status create_volume(vr_ctx ctx, const int dims[3], vr_dtype storage, const v
     vol->ctx = ctx;
     std::memcpy(vol->dims, dims, sizeof(vol->dims));
     vol->dtype = storage;
+    vol->octets = storage != VR_F32 && ctx->cell_layout == 1;
     const char *why = nullptr;
     if (!partition_plan(dims, part, vol->boxes, vol->tree, &why)) return fail(ctx, VR_ERR_ARG, why);
     const int nb = static_cast<int>(vol->boxes.size() / 6);
@@ -873,8 +876,8 @@ vr_status create_volume(vr_ctx ctx, const int dims[3], vr_dtype storage, const v
         }
     }
 
-    // brick-major haloed xy-quad storage of the held bricks, each 256-byte aligned
-    const size_t es = quad_size(storage);
+    // brick-major haloed xy-quad (or octet) storage of the held bricks, each 256-byte aligned
+    const size_t es = quad_size(storage, vol->octets);
     long long off_bytes = 0;
     vol->base.resize(nb);
     for (int b = 0; b < nb; ++b) {
@@ -1018,7 +1021,7 @@ vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_d
     if (st != VR_OK) return st;
     mp.partials = fr.d_part;
     mp.sample_counter = nullptr;
-    VR_LAUNCH(ctx, launch_march(mp, vol->dtype, s));
+    VR_LAUNCH(ctx, launch_march(mp, vol->kind(), s));
     if (fr.total_px > ctx->gpart_cap) {
         cudaFree(ctx->d_gpart);
         ctx->d_gpart = nullptr;
@@ -1046,7 +1049,7 @@ vr_status vr_render_backward(vr_ctx ctx, vr_volume vol, const float *grad_rgba_d
     ga.grad_vol = grad_density_dev;
     for (int a = 0; a < 3; ++a) ga.N[a] = vol->dims[a];
     ga.error = ctx->d_error;
-    VR_LAUNCH(ctx, launch_march_grad(mp, ga, vol->dtype, s));
+    VR_LAUNCH(ctx, launch_march_grad(mp, ga, vol->kind(), s));
     return VR_OK;
 }
 
@@ -1083,12 +1086,15 @@ vr_status vr_volume_read_brick(vr_volume vol, int brick, void *dst, size_t bytes
     const size_t n = static_cast<size_t>(sx) * sy * sz * es;
     if (bytes < n) return fail(vol->ctx, VR_ERR_ARG, "destination too small");
     const long long nq = brick_quads(bx);
-    std::vector<unsigned char> q(static_cast<size_t>(nq) * 4 * es);
+    const size_t per = vol->octets ? 8 : 4;  // voxels per storage element
+    std::vector<unsigned char> q(static_cast<size_t>(nq) * per * es);
     DeviceGuard g(vol->ctx->device);
     VR_CUDA(vol->ctx, cudaMemcpy(q.data(), static_cast<const char *>(vol->d_data) +
-                                               vol->base[brick] * static_cast<long long>(4 * es),
+                                               vol->base[brick] * static_cast<long long>(per * es),
                                  q.size(), cudaMemcpyDeviceToHost));
-    // voxel (i,j,k) is component (i==sx-1) + 2*(j==sy-1) of quad (min(i,sx-2), min(j,sy-2), k)
+    // voxel (i,j,k) is component (i==sx-1) + 2*(j==sy-1) of quad (min(i,sx-2), min(j,sy-2), k);
+    // with octets, quad k is the first half of element k, or for the last plane
+    // the second half of element k-1
     const int qx = sx - 1, qy = sy - 1, nbx = sx / 2, nby = sy / 2;
     unsigned char *out = static_cast<unsigned char *>(dst);
     for (int k = 0; k < sz; ++k)
@@ -1096,7 +1102,9 @@ vr_status vr_volume_read_brick(vr_volume vol, int brick, void *dst, size_t bytes
             for (int i = 0; i < sx; ++i) {
                 const int ii = std::min(i, qx - 1), jj = std::min(j, qy - 1);
                 const int c = (i == sx - 1 ? 1 : 0) + (j == sy - 1 ? 2 : 0);
-                const size_t src = static_cast<size_t>(quad_index(ii, jj, k, nbx, nby)) * 4 + c;
+                const bool upper = vol->octets && k == sz - 1;
+                const int kk = upper ? k - 1 : k;
+                const size_t src = static_cast<size_t>(quad_index(ii, jj, kk, nbx, nby)) * per + (upper ? 4 : 0) + c;
                 const size_t o = (static_cast<size_t>(k) * sy + j) * sx + i;
                 std::memcpy(out + o * es, q.data() + src * es, es);
             }
@@ -1288,6 +1296,14 @@ vr_status vr_composite_images(vr_ctx ctx, int n, const float *const *images_dev,
     ip.out = reinterpret_cast<float4 *>(out_dev);
     DeviceGuard g(ctx->device);
     VR_LAUNCH(ctx, launch_composite_images(ip, static_cast<cudaStream_t>(stream)));
+    return VR_OK;
+}
+
+vr_status vr_set_cell_layout(vr_ctx ctx, int layout)
+{
+    if (!ctx) return VR_ERR_ARG;
+    if (layout != 0 && layout != 1) return fail(ctx, VR_ERR_ARG, "cell layout 0 (xy-quads) or 1 (octets)");
+    ctx->cell_layout = layout;
     return VR_OK;
 }
 

@@ -10,6 +10,13 @@
 namespace vr {
 
 constexpr int kMaxBricks = VR_MAX_BRICKS;
+
+// Brick storage kind: the storage type and the cell layout -- xy-quads (four
+// voxels of one plane per element; two loads per sample) or, for the 16-bit
+// types, octets (both planes of a cell, 16 bytes per element; one load per
+// sample). The first three equal vr_dtype's values.
+enum StorageKind { kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2, kStoreBF16Oct = 3, kStoreF16Oct = 4 };
+inline int storage_kind(vr_dtype t, bool octets) { return static_cast<int>(t) + (octets && t != VR_F32 ? 2 : 0); }
 constexpr int kMaxFactors = 8;
 
 // Work item of the no-allocation march: 16 x 8 pixels per 128-thread block,
@@ -213,18 +220,19 @@ struct StagedBricks {
 };
 
 // Launchers (vr_kernels.cu). They return the launch's cudaError_t.
-cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s);
-cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s);
-cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out, cudaStream_t s);
+// `kind` is a StorageKind.
+cudaError_t launch_pack(const PackParams &p, int kind, cudaStream_t s);
+cudaError_t launch_march(const MarchParams &p, int kind, cudaStream_t s);
+cudaError_t launch_march_cycle(const MarchParams &p, int kind, float4 *out, cudaStream_t s);
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s);
 cudaError_t launch_composite_images(const ImagesParams &p, cudaStream_t s);
 // Tile masks of p (p.tile_mask) for frames whose march did not write them.
 cudaError_t launch_tile_masks(const CompositeParams &p, cudaStream_t s);
 cudaError_t launch_composite_grad(const CompositeGradParams &p, cudaStream_t s);
-cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, vr_dtype dtype, cudaStream_t s);
+cudaError_t launch_march_grad(const MarchParams &p, const GradArgs &g, int kind, cudaStream_t s);
 // Persistent batched kernel: cooperative launch of `blocks` blocks of 128 threads.
-cudaError_t launch_batch(const BatchParams &p, vr_dtype dtype, int blocks, cudaStream_t s);
-int batch_max_blocks_per_sm(vr_dtype dtype);
+cudaError_t launch_batch(const BatchParams &p, int kind, int blocks, cudaStream_t s);
+int batch_max_blocks_per_sm(int kind);
 // Staged march and the scalar brick pack (vr_staged.cu).
 cudaError_t launch_march_staged(const MarchParams &p, const StagedBricks &sb, cudaStream_t s);
 cudaError_t launch_scalar_pack(const PackParams &p, cudaStream_t s);

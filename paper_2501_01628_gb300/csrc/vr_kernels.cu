@@ -58,7 +58,16 @@ __global__ void __launch_bounds__(256) pack_kernel(const __grid_constant__ PackP
         const float *plane = p.src + static_cast<long long>(gz) * p.N[1] * p.N[0];
         const float *r0 = plane + static_cast<long long>(gy0) * p.N[0];
         const float *r1 = plane + static_cast<long long>(gy1) * p.N[0];
-        dst[q] = Quad<T>::make(__ldg(r0 + gx0), __ldg(r0 + gx1), __ldg(r1 + gx0), __ldg(r1 + gx1));
+        if constexpr (Quad<T>::octet) {  // plane lz and plane lz + 1 in one element
+            const int gz1 = min(max(B.lo[2] + lz, 0), p.N[2] - 1);
+            const float *plane1 = p.src + static_cast<long long>(gz1) * p.N[1] * p.N[0];
+            const float *s0 = plane1 + static_cast<long long>(gy0) * p.N[0];
+            const float *s1 = plane1 + static_cast<long long>(gy1) * p.N[0];
+            dst[q] = Quad<T>::make8(__ldg(r0 + gx0), __ldg(r0 + gx1), __ldg(r1 + gx0), __ldg(r1 + gx1),
+                                    __ldg(s0 + gx0), __ldg(s0 + gx1), __ldg(s1 + gx0), __ldg(s1 + gx1));
+        } else {
+            dst[q] = Quad<T>::make(__ldg(r0 + gx0), __ldg(r0 + gx1), __ldg(r1 + gx0), __ldg(r1 + gx1));
+        }
     }
 }
 
@@ -280,19 +289,21 @@ __global__ void __launch_bounds__(256) composite_images_kernel(const __grid_cons
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_pack(const PackParams &p, vr_dtype dtype, cudaStream_t s)
+cudaError_t launch_pack(const PackParams &p, int kind, cudaStream_t s)
 {
     if (p.n_blocks <= 0) return cudaSuccess;
-    switch (dtype) {
-    case VR_F32: pack_kernel<float><<<p.n_blocks, 256, 0, s>>>(p); break;
-    case VR_BF16: pack_kernel<__nv_bfloat16><<<p.n_blocks, 256, 0, s>>>(p); break;
-    case VR_F16: pack_kernel<__half><<<p.n_blocks, 256, 0, s>>>(p); break;
+    switch (kind) {
+    case kStoreF32: pack_kernel<float><<<p.n_blocks, 256, 0, s>>>(p); break;
+    case kStoreBF16: pack_kernel<__nv_bfloat16><<<p.n_blocks, 256, 0, s>>>(p); break;
+    case kStoreF16: pack_kernel<__half><<<p.n_blocks, 256, 0, s>>>(p); break;
+    case kStoreBF16Oct: pack_kernel<dev::Octet<__nv_bfloat16>><<<p.n_blocks, 256, 0, s>>>(p); break;
+    case kStoreF16Oct: pack_kernel<dev::Octet<__half>><<<p.n_blocks, 256, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s)
+cudaError_t launch_march(const MarchParams &p, int kind, cudaStream_t s)
 {
     if (p.n_items + p.mask_blocks <= 0) return cudaSuccess;
     const int grid = p.n_items + p.mask_blocks;
@@ -303,17 +314,19 @@ cudaError_t launch_march(const MarchParams &p, vr_dtype dtype, cudaStream_t s)
                   : (march_kernel<T, false, true><<<grid, 128, 0, s>>>(p), 0))                     \
          : (count ? (march_kernel<T, true, false><<<grid, 128, 0, s>>>(p), 0)                      \
                   : (march_kernel<T, false, false><<<grid, 128, 0, s>>>(p), 0)))
-    switch (dtype) {
-    case VR_F32: VR_MARCH(float); break;
-    case VR_BF16: VR_MARCH(__nv_bfloat16); break;
-    case VR_F16: VR_MARCH(__half); break;
+    switch (kind) {
+    case kStoreF32: VR_MARCH(float); break;
+    case kStoreBF16: VR_MARCH(__nv_bfloat16); break;
+    case kStoreF16: VR_MARCH(__half); break;
+    case kStoreBF16Oct: VR_MARCH(dev::Octet<__nv_bfloat16>); break;
+    case kStoreF16Oct: VR_MARCH(dev::Octet<__half>); break;
     default: return cudaErrorInvalidValue;
     }
 #undef VR_MARCH
     return cudaGetLastError();
 }
 
-cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out, cudaStream_t s)
+cudaError_t launch_march_cycle(const MarchParams &p, int kind, float4 *out, cudaStream_t s)
 {
     if (p.W <= 0 || p.H <= 0) return cudaSuccess;
     const dim3 grid((p.W + p.tile_w - 1) / p.tile_w, (p.H + p.tile_h - 1) / p.tile_h);
@@ -324,10 +337,12 @@ cudaError_t launch_march_cycle(const MarchParams &p, vr_dtype dtype, float4 *out
                   : (march_cycle_kernel<T, false, true><<<grid, 128, 0, s>>>(p, out), 0))              \
          : (count ? (march_cycle_kernel<T, true, false><<<grid, 128, 0, s>>>(p, out), 0)               \
                   : (march_cycle_kernel<T, false, false><<<grid, 128, 0, s>>>(p, out), 0)))
-    switch (dtype) {
-    case VR_F32: VR_CYCLE(float); break;
-    case VR_BF16: VR_CYCLE(__nv_bfloat16); break;
-    case VR_F16: VR_CYCLE(__half); break;
+    switch (kind) {
+    case kStoreF32: VR_CYCLE(float); break;
+    case kStoreBF16: VR_CYCLE(__nv_bfloat16); break;
+    case kStoreF16: VR_CYCLE(__half); break;
+    case kStoreBF16Oct: VR_CYCLE(dev::Octet<__nv_bfloat16>); break;
+    case kStoreF16Oct: VR_CYCLE(dev::Octet<__half>); break;
     default: return cudaErrorInvalidValue;
     }
 #undef VR_CYCLE

@@ -93,6 +93,7 @@ struct vr_ctx_s {
     float opc_ref = 0.0f;          // opacity-correction reference step in voxels (0: off)
     int packet_width = 4;          // ray packet of the march: pw x (32/pw) pixels per warp
     bool staging = false;          // march float32 volumes with brick slabs staged in shared memory
+    int cell_layout = 0;           // 16-bit volumes created next: 0 xy-quads, 1 octets (vr_set_cell_layout)
     unsigned long long *d_counter = nullptr;
     int *d_error = nullptr;        // device error word (vr_sync reports and clears it)
     bool count_samples = false;
@@ -141,13 +142,15 @@ struct vr_volume_s {
     // render as empty partials (the identity of "over").
     std::vector<char> held;
     bool holds(int b) const { return held.empty() || held[b]; }
+    bool octets = false;           // 16-bit storage with both planes of a cell per element
+    int kind() const { return vr::storage_kind(dtype, octets); }
 };
 
 namespace vr {
 namespace host {
 
 size_t elem_size(vr_dtype t);
-size_t quad_size(vr_dtype t);
+size_t quad_size(vr_dtype t, bool octets = false);
 long long brick_quads(const int *bx);
 vr_status fail(vr_ctx ctx, vr_status s, const std::string &msg);
 vr_status cuda_fail(vr_ctx ctx, cudaError_t e, const char *what);

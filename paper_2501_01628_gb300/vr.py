@@ -40,7 +40,7 @@ EXPORTS = (
     "vr_set_opacity_correction", "vr_volume_update_async", "vr_set_packet_width",
     "vr_set_host_output_async", "vr_mesh_create", "vr_mesh_release", "vr_mesh_info",
     "vr_render_mesh_frame", "vr_debug_inject_fault", "vr_batch_debug_wait", "vr_set_march_staging",
-    "vr_volume_create_share", "vr_composite_images",
+    "vr_volume_create_share", "vr_composite_images", "vr_set_cell_layout",
 )
 
 
@@ -108,6 +108,7 @@ _SIG = {
     "vr_set_opacity_correction": (_I, [_P, ctypes.c_float]),
     "vr_set_packet_width": (_I, [_P, _I]),
     "vr_set_march_staging": (_I, [_P, _I]),
+    "vr_set_cell_layout": (_I, [_P, _I]),
     "vr_set_host_output_async": (_I, [_P, _I]),
     "vr_render_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "vr_partition_boxes": (_I, [_P, ctypes.POINTER(vr_partition), _P, _P]),
@@ -494,6 +495,12 @@ def vr_set_march_staging(ctx, on: bool):
     """Float32 volumes created afterwards keep a scalar brick copy and march with
     brick slabs staged in shared memory (same image, different speed)."""
     _check(lib().vr_set_march_staging(ctx, int(bool(on))), ctx, "vr_set_march_staging")
+
+
+def vr_set_cell_layout(ctx, layout: int):
+    """16-bit volumes created afterwards: 0 xy-quads (default), 1 octets (both
+    planes of a cell per element: one load per sample, twice the memory)."""
+    _check(lib().vr_set_cell_layout(ctx, int(layout)), ctx, "vr_set_cell_layout")
 
 
 def vr_set_render_mode(ctx, mode: int):

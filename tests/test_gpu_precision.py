@@ -73,3 +73,73 @@ def test_precision_workload_crop(vr, tfkind):
         compare_envelope(got, env)
         mean_total = float(np.mean(np.abs(got - ref_total)))
         assert mean_total <= MEAN_TOTAL_TOL, (storage, mean_total)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_octet_layout_equals_quads(vr, storage):
+    """16-bit octets (both planes of a cell per element) hold the same values as
+    16-bit xy-quads and feed the same arithmetic: identical packed voxels,
+    identical images in both frame algorithms and in a batch, the same
+    gradients (up to the order of float atomics), and the oracle's bar on the
+    quantised values."""
+    import torch
+    rng = np.random.default_rng(61)
+    n = 40
+    vol = synth.blob_volume(n, synth.draw_blobs(rng, 6))
+    vol += rng.uniform(0, 0.05, vol.shape).astype(np.float32)
+    tf = synth.random_tf(rng, alpha_max=0.2)
+    lo, hi = synth.volume_range(vol)
+    part = dict(kind="kd", n_bricks=6, cut_fracs=rng.uniform(0.3, 0.7, 5))
+    cams = [synth.orbit_camera(72, 53, az, elevation_deg=el) for az, el in ((25, 20), (160, -35), (290, 50))]
+    g_np = rng.standard_normal((53, 72, 4)).astype(np.float32)  # one upstream gradient for both layouts
+    res = {}
+    for layout in (0, 1):
+        ctx = vr.vr_create(0)
+        v = None
+        try:
+            vr.vr_set_cell_layout(ctx, layout)
+            v = vr.vr_volume_create(ctx, vol, storage, part)
+            vr.vr_set_transfer_function(ctx, tf, lo, hi)
+            bricks = [vr.vr_volume_read_brick(v, b, storage) for b in range(6)]
+            imgs = []
+            for mode, ert in ((0, 1.0), (0, 0.95), (1, 0.95)):
+                vr.vr_set_render_mode(ctx, mode)
+                vr.vr_set_render_params(ctx, 0.5, ert)
+                for cam in cams:
+                    vr.vr_set_camera(ctx, cam)
+                    o = torch.empty((cam["height"], cam["width"], 4), device="cuda")
+                    vr.vr_render_frame(ctx, v, o)
+                    imgs.append(o)
+            vr.vr_set_render_mode(ctx, 0)
+            vr.vr_set_render_params(ctx, 0.5, 1.0)
+            out = torch.empty((len(cams), 53, 72, 4), device="cuda")
+            b = vr.vr_batch_create(ctx, [v], cams, out, vmins=[lo], vmaxs=[hi])
+            vr.vr_batch_launch(b)
+            vr.vr_sync(ctx)
+            vr.vr_batch_release(b)
+            vr.vr_set_camera(ctx, cams[0])
+            g_img = torch.from_numpy(g_np).cuda()
+            gtf = torch.zeros((tf.shape[0], 4), device="cuda")
+            gvol = torch.zeros((n, n, n), device="cuda")
+            vr.vr_render_backward(ctx, v, g_img, gtf, gvol)
+            vr.vr_sync(ctx)
+            res[layout] = (bricks, imgs, out.clone(), gtf.cpu().numpy(), gvol.cpu().numpy())
+        finally:
+            if v is not None:
+                vr.vr_volume_release(v)
+            vr.vr_destroy(ctx)
+    (qb, qi, qbat, qgt, qgv), (ob, oi, obat, ogt, ogv) = res[0], res[1]
+    for a, b in zip(qb, ob):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(qi, oi):
+        assert torch.equal(a, b), float((a - b).abs().max())
+    assert torch.equal(qbat, obat)
+    for w in range(len(cams)):  # the batch renders equal the plain ones
+        assert torch.equal(obat[w], oi[w])
+    for a, b in ((qgt, ogt), (qgv, ogv)):
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a) + 1e-12
+    q = synth.quantize(vol, storage)
+    boxes = vr.vr_partition_boxes((n,) * 3, part)
+    code = oracle.BF16 if storage == "bf16" else oracle.F16
+    compare_envelope(oi[0].cpu().numpy().astype(np.float64),
+                     oracle_env(q, boxes, tf, lo, hi, cams[0], dtype=code))
