@@ -208,8 +208,8 @@ vr_status vr_set_packet_width(vr_ctx ctx, int packet_width);
  * memory, slab by slab in depth (bulk asynchronous copies, cp.async.bulk,
  * completing on an mbarrier, two stages per block), instead of reading
  * xy-quads through L1. The image is the same bit for bit; the speed differs
- * (the benchmark spec's staging of brick tiles for ray packets; measured against the
- * xy-quad march on the orbit workload). Volumes without the scalar copy (other
+ * (brick tiles staged for ray packets; on the 1080p orbit workload it is
+ * slower than the xy-quad march). Volumes without the scalar copy (other
  * storage types, or created while staging was off) keep the xy-quad march.
  * Each bounded wait for a staged slab that gives up makes the next vr_sync
  * return VR_ERR_TIMEOUT. */
