@@ -332,6 +332,7 @@ bool camera_valid(const vr_camera *cam)
 // Pack every brick of `vol` from the device float32 volume `dsrc`.
 cudaError_t pack_bricks(vr_volume vol, const float *dsrc, cudaStream_t s)
 {
+    vol->ctx->input_seq++;  // a pipelined march must not overlap this pack
     const size_t es = quad_size(vol->dtype, vol->octets);
     const int nb = static_cast<int>(vol->boxes.size() / 6);
     static thread_local PackParams pp;
@@ -509,7 +510,7 @@ void timing_end(vr_ctx ctx, int idx, cudaStream_t s)
     if (idx >= 0) cudaEventRecord(ctx->timed[idx].b, s);
 }
 
-vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s)
+vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s, bool after_composite = false)
 {
     static thread_local MarchParams mp;  // ~12 KB: keep off the stack
     vr_status st = prepare_frame(ctx, vol, fr, mp);
@@ -532,14 +533,14 @@ vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s)
         }
         VR_LAUNCH(ctx, launch_march_staged(mp, sb, s));
     } else {
-        VR_LAUNCH(ctx, launch_march(mp, vol->kind(), s));
+        VR_LAUNCH(ctx, launch_march(mp, vol->kind(), s, after_composite));
     }
     timing_end(ctx, t, s);
     fr.masks_ready = true;
     return VR_OK;
 }
 
-vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s)
+vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s, int max_blocks = 0)
 {
     static thread_local CompositeParams cp;
     std::memset(&cp, 0, sizeof(cp));
@@ -579,7 +580,7 @@ vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s)
         fr.masks_ready = true;
     }
     const int t = timing_begin(ctx, 1, s);
-    VR_LAUNCH(ctx, launch_composite(cp, s));
+    VR_LAUNCH(ctx, launch_composite(cp, s, max_blocks));
     timing_end(ctx, t, s);
     return VR_OK;
 }
@@ -679,6 +680,39 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
     return VR_OK;
 }
 
+// A sort-last frame into the caller's image. Pipelined frames (device output,
+// kernel timing off, the quad march) alternate between the context's two
+// frames and composite with a persistent grid of two blocks per multiprocessor,
+// which is resident early in the march's tail; its blocks signal at their start,
+// so the next frame's march (launched as a programmatic dependent when nothing
+// it reads before its waits has changed, on the same stream) can fill the
+// multiprocessors as this frame's march drains. Every write of that march waits
+// for this composite's completion, and the pool it writes was last read by the
+// frame before, whose composite precedes this one in the stream.
+vr_status render_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cudaStream_t s)
+{
+    if (!out) return fail(ctx, VR_ERR_ARG, "null output");
+    const bool pipe = ctx->pipelining && out_on_device && !ctx->timing && !(ctx->staging && vol->d_scalar);
+    if (!pipe) {
+        ctx->pipe_ready = false;
+        vr_status st = march(ctx, vol, ctx->frame, s);
+        if (st != VR_OK) return st;
+        return composite_to(ctx, ctx->frame, out, out_on_device, s);
+    }
+    vr_frame_s &fr = ctx->frame_next ? ctx->frame2 : ctx->frame;
+    const bool after = ctx->pipe_ready && ctx->pipe_stream == s && ctx->pipe_seq == ctx->input_seq;
+    ctx->pipe_ready = false;  // until this frame's composite is launched
+    vr_status st = march(ctx, vol, fr, s, after);
+    if (st != VR_OK) return st;
+    st = composite(ctx, fr, reinterpret_cast<float4 *>(out), s, ctx->sms > 0 ? 2 * ctx->sms : 0);
+    if (st != VR_OK) return st;
+    ctx->pipe_ready = true;
+    ctx->pipe_stream = s;
+    ctx->pipe_seq = ctx->input_seq;
+    ctx->frame_next ^= 1;
+    return VR_OK;
+}
+
 }  // namespace host
 }  // namespace vr
 
@@ -757,6 +791,11 @@ vr_status vr_create(int cuda_device, vr_ctx *out)
         return VR_ERR_CUDA;
     }
     ctx->frame.owned_by_ctx = true;
+    ctx->frame2.owned_by_ctx = true;
+    if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->sms = 0;
+    }
     *out = ctx;
     return VR_OK;
 }
@@ -772,6 +811,7 @@ vr_status vr_destroy(vr_ctx ctx)
     cudaFree(ctx->d_error);
     cudaFree(ctx->d_gpart);
     cudaFree(ctx->frame.d_part);
+    cudaFree(ctx->frame2.d_part);
     cudaFree(ctx->d_img);
     if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
     for (int i = 0; i < 2; ++i) {
@@ -1138,6 +1178,7 @@ vr_status vr_set_transfer_function(vr_ctx ctx, const float *rgba, int n, float v
             pairs[8 * i + c] = a;
             pairs[8 * i + 4 + c] = b - a;
         }
+    ctx->input_seq++;  // a pipelined march must not read the table across this upload
     VR_CUDA(ctx, cudaMemcpy(ctx->d_tf, pairs.data(), pairs.size() * sizeof(float), cudaMemcpyHostToDevice));
     ctx->ntf = n;
     ctx->vmin = vmin;
@@ -1256,9 +1297,15 @@ vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (ctx->mode == 1) return cycle_to(ctx, vol, out_rgba, out_on_device, s);
-    vr_status st = march(ctx, vol, ctx->frame, s);
-    if (st != VR_OK) return st;
-    return composite_to(ctx, ctx->frame, out_rgba, out_on_device, s);
+    return render_to(ctx, vol, out_rgba, out_on_device, s);
+}
+
+vr_status vr_set_frame_pipelining(vr_ctx ctx, int on)
+{
+    if (!ctx) return VR_ERR_ARG;
+    ctx->pipelining = on != 0;
+    ctx->pipe_ready = false;
+    return VR_OK;
 }
 
 vr_status vr_set_opacity_correction(vr_ctx ctx, float ref_step_voxels)

@@ -222,9 +222,13 @@ struct StagedBricks {
 // Launchers (vr_kernels.cu). They return the launch's cudaError_t.
 // `kind` is a StorageKind.
 cudaError_t launch_pack(const PackParams &p, int kind, cudaStream_t s);
-cudaError_t launch_march(const MarchParams &p, int kind, cudaStream_t s);
+// after_composite: launch as a programmatic dependent of the preceding kernel
+// (the previous pipelined frame's composite); see march_kernel.
+cudaError_t launch_march(const MarchParams &p, int kind, cudaStream_t s, bool after_composite = false);
 cudaError_t launch_march_cycle(const MarchParams &p, int kind, float4 *out, cudaStream_t s);
-cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s);
+// max_blocks > 0: a grid of at most that many blocks, each compositing tiles in
+// turn; 0: one block per tile.
+cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s, int max_blocks = 0);
 cudaError_t launch_composite_images(const ImagesParams &p, cudaStream_t s);
 // Tile masks of p (p.tile_mask) for frames whose march did not write them.
 cudaError_t launch_tile_masks(const CompositeParams &p, cudaStream_t s);

@@ -92,7 +92,13 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     // this grid is running; it reads the masks and partials only after this
     // grid has completed
     asm volatile("griddepcontrol.launch_dependents;");
+    // Launched as a programmatic dependent of the previous frame's composite
+    // (pipelined frames), this grid reads only the bricks and the table before
+    // the waits below; its writes (masks, partials) go to a pool that the frame
+    // before the previous one read, and wait for the preceding grid's completion.
+    // Outside such a launch the waits return at once.
     if (static_cast<int>(blockIdx.x) < p.mask_blocks) {  // the composite's tile masks
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         dev::write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.mask_tiles_x, p.mask_tiles_y, p.nb, p.order,
                         [&](int b) { return make_int4(p.b[b].rect[0], p.b[b].rect[1], p.b[b].rect[2],
                                                       p.b[b].rect[3]); },
@@ -118,6 +124,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
                                       p.count_error);
     // the composite reads the partial next: keep it in L2 ahead of the streamed bricks
     float4 *dst = p.partials + B.poff + static_cast<long long>(ry) * B.rect[2] + rx;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     unsigned long long policy;
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
     asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "f"(c.x), "f"(c.y),
@@ -199,12 +206,18 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
 {
     constexpr int kBatch = 4;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int tx0 = blockIdx.x * kCompW, ty0 = blockIdx.y * kCompTileH;
-    const int px = tx0 + threadIdx.x;
+    // a march launched after this grid as its programmatic dependent (the next
+    // pipelined frame) may start once every block of this grid is running
+    asm volatile("griddepcontrol.launch_dependents;");
     // launched as a programmatic dependent of the march: wait for the preceding
     // grid's completion and memory (the masks and partials are its output)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const uint4 mk = __ldg(p.tile_mask + blockIdx.y * p.tiles_x + blockIdx.x);
+    const int ntiles = p.tiles_x * p.tiles_y;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {  // one tile per block, or a persistent grid
+    const int tyi = tile / p.tiles_x;
+    const int tx0 = (tile - tyi * p.tiles_x) * kCompW, ty0 = tyi * kCompTileH;
+    const int px = tx0 + threadIdx.x;
+    const uint4 mk = __ldg(p.tile_mask + tile);
     for (int half = 0; half < kCompRows; ++half) {
         const int py = ty0 + threadIdx.y + kCompH * half;
         unsigned long long r0 = static_cast<unsigned long long>(mk.x) | (static_cast<unsigned long long>(mk.y) << 32);
@@ -266,6 +279,7 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
             __stcs(p.out + static_cast<long long>(py) * p.W + px, res);
         }
     }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -303,27 +317,37 @@ cudaError_t launch_pack(const PackParams &p, int kind, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_march(const MarchParams &p, int kind, cudaStream_t s)
+cudaError_t launch_march(const MarchParams &p, int kind, cudaStream_t s, bool after_composite)
 {
     if (p.n_items + p.mask_blocks <= 0) return cudaSuccess;
     const int grid = p.n_items + p.mask_blocks;
     const bool count = p.sample_counter != nullptr;
     const bool opc = p.opc_ratio != 1.0f;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_composite ? 1 : 0;
 #define VR_MARCH(T)                                                                                     \
-    (opc ? (count ? (march_kernel<T, true, true><<<grid, 128, 0, s>>>(p), 0)                       \
-                  : (march_kernel<T, false, true><<<grid, 128, 0, s>>>(p), 0))                     \
-         : (count ? (march_kernel<T, true, false><<<grid, 128, 0, s>>>(p), 0)                      \
-                  : (march_kernel<T, false, false><<<grid, 128, 0, s>>>(p), 0)))
+    (opc ? (count ? cudaLaunchKernelEx(&cfg, march_kernel<T, true, true>, p)                       \
+                  : cudaLaunchKernelEx(&cfg, march_kernel<T, false, true>, p))                     \
+         : (count ? cudaLaunchKernelEx(&cfg, march_kernel<T, true, false>, p)                      \
+                  : cudaLaunchKernelEx(&cfg, march_kernel<T, false, false>, p)))
+    cudaError_t e = cudaErrorInvalidValue;
     switch (kind) {
-    case kStoreF32: VR_MARCH(float); break;
-    case kStoreBF16: VR_MARCH(__nv_bfloat16); break;
-    case kStoreF16: VR_MARCH(__half); break;
-    case kStoreBF16Oct: VR_MARCH(dev::Octet<__nv_bfloat16>); break;
-    case kStoreF16Oct: VR_MARCH(dev::Octet<__half>); break;
+    case kStoreF32: e = VR_MARCH(float); break;
+    case kStoreBF16: e = VR_MARCH(__nv_bfloat16); break;
+    case kStoreF16: e = VR_MARCH(__half); break;
+    case kStoreBF16Oct: e = VR_MARCH(dev::Octet<__nv_bfloat16>); break;
+    case kStoreF16Oct: e = VR_MARCH(dev::Octet<__half>); break;
     default: return cudaErrorInvalidValue;
     }
 #undef VR_MARCH
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_march_cycle(const MarchParams &p, int kind, float4 *out, cudaStream_t s)
@@ -369,14 +393,15 @@ cudaError_t launch_tile_masks(const CompositeParams &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s)
+cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s, int max_blocks)
 {
     if (p.W <= 0 || p.H <= 0) return cudaSuccess;
     if (p.tiles_x != (p.W + kCompW - 1) / kCompW || p.tiles_y != (p.H + kCompTileH - 1) / kCompTileH ||
         !p.tile_mask)
         return cudaErrorInvalidValue;
+    const int tiles = p.tiles_x * p.tiles_y;
     dim3 block(kCompW, kCompH);
-    dim3 grid(p.tiles_x, p.tiles_y);
+    dim3 grid(max_blocks > 0 ? std::min(tiles, max_blocks) : tiles);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;

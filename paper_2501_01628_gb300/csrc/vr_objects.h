@@ -100,6 +100,19 @@ struct vr_ctx_s {
     float4 *d_gpart = nullptr;     // partial gradients (backward), partial-pool layout
     long long gpart_cap = 0;
     vr_frame_s frame;              // context-owned frame for vr_render_frame
+    // Pipelined frames (vr_set_frame_pipelining): vr_render_frame into device
+    // memory alternates between `frame` and `frame2`, and its march may start
+    // in the previous frame's composite when nothing the march reads before its
+    // waits (bricks, table) has been written since that composite was launched
+    // on the same stream: input_seq counts brick packs and table uploads.
+    bool pipelining = true;
+    vr_frame_s frame2;
+    int frame_next = 0;
+    int sms = 0;                   // multiprocessors of the device (persistent composite grid)
+    unsigned long long input_seq = 0;
+    bool pipe_ready = false;
+    cudaStream_t pipe_stream = nullptr;
+    unsigned long long pipe_seq = 0;
     float4 *d_img = nullptr;       // staging for host outputs
     long long img_cap = 0;
     // asynchronous host output: two staging images, copies on their own stream
