@@ -214,20 +214,22 @@ vr_status vr_set_packet_width(vr_ctx ctx, int packet_width);
  * Each bounded wait for a staged slab that gives up makes the next vr_sync
  * return VR_ERR_TIMEOUT. */
 vr_status vr_set_march_staging(vr_ctx ctx, int on);
-/* Pipelined frames (on by default). With on != 0, vr_render_frame calls that
- * write device memory alternate between two context-owned frames (partial
- * pools), and the composite runs as a persistent grid (two blocks per
- * multiprocessor) that signals at its start, so the next such call's march can
- * start while this frame's march drains and its composite runs (programmatic
- * dependent launch; Sec. 3's render-then-composite per frame, overlapped
- * between consecutive frames). Ordering stays that of the stream: every write
- * of the overlapping march (its partials and tile masks) waits for the
- * previous composite to complete, and the march overlaps only when the
+/* Pipelined frames (on by default). With on != 0, vr_render_frame calls into
+ * device memory, or into host memory with asynchronous host output
+ * (vr_set_host_output_async), alternate between two context-owned frames
+ * (partial pools), and the composite runs as a persistent grid of two blocks
+ * per multiprocessor that signals at its start, so the next such call's march
+ * can start while this frame's march drains and its composite runs
+ * (programmatic dependent launch; Sec. 3's render-then-composite per frame,
+ * overlapped between consecutive frames). Ordering stays that of the stream:
+ * every write of the overlapping march (its partials and tile masks) waits for
+ * the previous composite to complete, and the march overlaps only when the
  * previous pipelined frame was launched on the same stream and no brick pack
  * (volume create or update) and no transfer-function upload of this context
- * came in between. Images are bit-identical either way. Kernel timing, host
- * outputs and the staged march use the plain sequence (one frame, one block
- * per composite tile). Costs a second partial pool per context. */
+ * came in between. Images are bit-identical either way. Kernel timing,
+ * synchronous host outputs and the staged march use the plain sequence (one
+ * frame, one block per composite tile). Costs a second partial pool per
+ * context. */
 vr_status vr_set_frame_pipelining(vr_ctx ctx, int on);
 /* Cell layout of bfloat16 / float16 volumes created afterwards (the precision
  * form: 16-bit storage, float32 arithmetic). 0 (default): xy-quads, four

@@ -680,8 +680,8 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
     return VR_OK;
 }
 
-// A sort-last frame into the caller's image. Pipelined frames (device output,
-// kernel timing off, the quad march) alternate between the context's two
+// A sort-last frame into the caller's image. Pipelined frames (device output
+// or asynchronous host output, kernel timing off, the quad march) alternate between the context's two
 // frames and composite with a persistent grid of two blocks per multiprocessor,
 // which is resident early in the march's tail; its blocks signal at their start,
 // so the next frame's march (launched as a programmatic dependent when nothing
@@ -692,7 +692,8 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
 vr_status render_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cudaStream_t s)
 {
     if (!out) return fail(ctx, VR_ERR_ARG, "null output");
-    const bool pipe = ctx->pipelining && out_on_device && !ctx->timing && !(ctx->staging && vol->d_scalar);
+    const bool pipe = ctx->pipelining && (out_on_device || ctx->host_async) && !ctx->timing &&
+                      !(ctx->staging && vol->d_scalar);
     if (!pipe) {
         ctx->pipe_ready = false;
         vr_status st = march(ctx, vol, ctx->frame, s);
@@ -704,7 +705,17 @@ vr_status render_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cu
     ctx->pipe_ready = false;  // until this frame's composite is launched
     vr_status st = march(ctx, vol, fr, s, after);
     if (st != VR_OK) return st;
-    st = composite(ctx, fr, reinterpret_cast<float4 *>(out), s, ctx->sms > 0 ? 2 * ctx->sms : 0);
+    const int blocks = ctx->sms > 0 ? 2 * ctx->sms : 0;
+    if (out_on_device) {
+        st = composite(ctx, fr, reinterpret_cast<float4 *>(out), s, blocks);
+    } else {  // one of the two staging images, copied on the copy stream
+        const long long px = static_cast<long long>(fr.W) * fr.H;
+        float4 *buf = nullptr;
+        int slot = -1;
+        st = host_staging(ctx, px, s, &buf, &slot);
+        if (st == VR_OK) st = composite(ctx, fr, buf, s, blocks);
+        if (st == VR_OK) st = host_copy(ctx, out, buf, slot, px, s);
+    }
     if (st != VR_OK) return st;
     ctx->pipe_ready = true;
     ctx->pipe_stream = s;

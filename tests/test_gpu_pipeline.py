@@ -238,3 +238,28 @@ def test_pipelined_paper_workload(vr):
         finally:
             _close(vr, ctx, v)
     _assert_equal(res[False], res[True])
+
+
+def test_pipelined_asynchronous_host_outputs(vr):
+    """Asynchronous host outputs (two staging images, copies on the copy stream)
+    in a pipelined sequence equal the plain sequence's device images."""
+    import torch
+    vol, tf, rng = _scene(seed=19)
+    part = dict(kind="grid", grid=(3, 2, 2))
+    cams = [synth.orbit_camera(88, 70, az, elevation_deg=15.0) for az in (10.0, 100.0, 190.0, 280.0, 10.0)]
+    ctx, v = _ctx(vr, vol, part, tf, False, schedule=(3, 4), ert=0.99)
+    try:
+        want = _sequence(vr, ctx, v, cams)
+    finally:
+        _close(vr, ctx, v)
+    ctx, v = _ctx(vr, vol, part, tf, True, schedule=(3, 4), ert=0.99)
+    try:
+        vr.vr_set_host_output_async(ctx, True)
+        hosts = [torch.full((c["height"], c["width"], 4), float("nan")).pin_memory() for c in cams]
+        for cam, h in zip(cams, hosts):
+            vr.vr_set_camera(ctx, cam)
+            vr.vr_render_frame(ctx, v, h)
+        vr.vr_sync(ctx)
+    finally:
+        _close(vr, ctx, v)
+    _assert_equal(want, hosts)
