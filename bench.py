@@ -591,7 +591,8 @@ def run_ours(a):
 
 def run_precision(a):
     """Precision form: the 1024^3 blob volume (seed 2, 64 kd bricks, 2048^2
-    perspective) stored as float32, bfloat16 and float16; frame time of each and,
+    perspective) stored as float32, bfloat16 and float16 (the 16-bit types as
+    xy-quads and as octets); frame time of each and,
     for the 16-bit forms, the error against the FP64 oracle on the centre 256^2
     crop (accumulation error: oracle on the same quantised values; total error:
     oracle on the float32 source)."""
@@ -615,8 +616,10 @@ def run_precision(a):
     out = torch.empty((2048, 2048, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     forms = {}
-    for storage in ("f32", "bf16", "f16"):
+    for form in ("f32", "bf16", "f16", "bf16_octets", "f16_octets"):
+        storage = form.split("_")[0]
         ctx = vr.vr_create(0)
+        vr.vr_set_cell_layout(ctx, 1 if form.endswith("octets") else 0)
         v = vr.vr_volume_create(ctx, vol_dev, storage, part)
         vr.vr_set_transfer_function(ctx, tf, lo, hi)
         vr.vr_set_render_params(ctx, 0.5, 1.0)
@@ -649,10 +652,10 @@ def run_precision(a):
                                       dtype=code)["img"]
                 e["err_accumulation_max"] = float(np.max(np.abs(img - ref_q)))
             f["tf_" + kind] = e
-        forms[storage] = f
+        forms[form] = f
         vr.vr_volume_release(v)
         vr.vr_destroy(ctx)
-    for s in ("bf16", "f16"):
+    for s in ("bf16", "f16", "bf16_octets", "f16_octets"):
         forms[s]["speedup_vs_f32"] = forms["f32"]["ms_per_frame"] / forms[s]["ms_per_frame"]
     line = dict(metric=METRIC, value=forms["bf16"]["samples_per_s"], unit=UNIT, n_gpus=1, steps=a.steps,
                 warmup=a.warmup, ms_per_step=forms["bf16"]["ms_per_frame"], higher_is_better=True,
