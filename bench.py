@@ -569,7 +569,7 @@ def run_ours(a):
                                          note="partial reads + image write / composite time, %s" % hbm_src)),
         kernel_ms=dict(march=march_ms, composite=comp_ms,
                        note="event pairs on every launch of %d frames over the orbit views; with timing on, "
-                            "frames run the plain sequence (composite: one block per 32x16 tile)" % kt_frames),
+                            "frames run the plain sequence (composite: one block per 32x8 tile)" % kt_frames),
         pipelining=dict(ms_per_frame=ms / K, plain_ms_per_frame=plain_ms / K,
                         speedup=plain_ms / ms,
                         note="timed region: pipelined frames (vr_set_frame_pipelining, the default): the "

@@ -450,7 +450,7 @@ vr_status vr_debug_inject_fault(int kind, int after);
  * masks and the transfer function live in one static device array of
  * VR_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
  * process exits. A frame whose partial images (16 bytes per pixel of every
- * brick's footprint rectangle) and tile masks (16 bytes per 32 x 16 pixels)
+ * brick's footprint rectangle) and tile masks (16 bytes per 32 x 8 pixels)
  * would exceed it is rejected with VR_ERR_ARG before any device work.
  *   - Works on the current CUDA device. Every call looks up the scratch's
  *     device address (cudaGetSymbolAddress) on that device, so the call stays

@@ -24,13 +24,12 @@ constexpr int kMaxFactors = 8;
 // parameter, MarchParams::pw).
 constexpr int kTileW = 16;
 constexpr int kTileH = 8;
-// Composite: 256-thread blocks of 32 x 8 threads. The forward composite gives a
-// block a tile of kCompRows such 32 x 8 halves, stacked (one brick list per
-// 32 x 16 tile); the composite adjoint takes 32 x 8 tiles.
+// Composite: 256-thread blocks of 32 x 8 threads, one thread per pixel of a
+// 32 x 8 image tile with one brick mask per tile (the composite adjoint takes the
+// same tiles).
 constexpr int kCompW = 32;
 constexpr int kCompH = 8;
-constexpr int kCompRows = 2;
-constexpr int kCompTileH = kCompH * kCompRows;  // forward composite tile: kCompW x kCompTileH pixels
+constexpr int kCompTileH = kCompH;  // forward composite tile: kCompW x kCompTileH pixels
 constexpr int kMaskThreads = 128;                // threads (tiles) per block of the tile-mask pass
 
 // Brick storage index of quad (i, j, k): quads are grouped in 2x2x2 blocks of

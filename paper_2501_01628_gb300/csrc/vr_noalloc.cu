@@ -24,7 +24,7 @@ namespace {
 
 // Scratch shared by every call on a device, held until the process exits:
 // [0, kTfBytes) transfer-function pairs, then the composite's tile masks (one
-// 16-byte mask per 32 x 16 tile of the image), then the partial images (float4).
+// 16-byte mask per 32 x 8 tile of the image), then the partial images (float4).
 constexpr size_t kScratchBytes = VR_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kTfBytes = 2 * 1024 * sizeof(float4);
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
