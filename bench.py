@@ -561,7 +561,11 @@ def run_ours(a):
         roofline_l1=dict(frac=recorded_value("l1_wavefronts_frac") if a.workload == "paper" else None,
                          unit="fraction of peak L1 data-pipe wavefronts",
                          note="ncu --set full on the march of this kernel code (null once the code changes): "
-                              "the L1/shared data pipe is the march's closest bound; see profiles/"),
+                              "the L1/shared data pipe is the march's busiest unit; see profiles/"),
+        roofline_issue=dict(frac=recorded_value("issue_active_frac") if a.workload == "paper" else None,
+                            unit="fraction of peak warp-instruction issue (smsp__issue_active)",
+                            note="ncu --set full on the march of this kernel code (null once the code changes): "
+                                 "the march is bound by issue and the latency of its dependent loads"),
         roofline_hbm=dict(march=dict(achieved=march_hbm_gbs, peak=hbm, unit="GB/s", frac=march_hbm_gbs / hbm,
                                      note="compulsory bytes (volume once + partial writes) / march time, %s"
                                           % hbm_src),
