@@ -673,10 +673,24 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
         st = host_staging(ctx, px, s, &dst, &slot);
         if (st != VR_OK) return st;
     }
+    // pipelined frames (see render_to): this frame's kernel may start in the
+    // previous frame's tail; it reads only the bricks and the table before it
+    // waits, and writes its image after the preceding grid completes
+    const bool pipe = ctx->pipelining && (out_on_device || ctx->host_async) && !ctx->timing;
+    const bool after = pipe && ctx->pipe_ready && ctx->pipe_stream == s && ctx->pipe_seq == ctx->input_seq;
+    ctx->pipe_ready = false;
     const int t = timing_begin(ctx, 0, s);
-    VR_LAUNCH(ctx, launch_march_cycle(mp, vol->kind(), dst, s));
+    VR_LAUNCH(ctx, launch_march_cycle(mp, vol->kind(), dst, s, after));
     timing_end(ctx, t, s);
-    if (!out_on_device) return host_copy(ctx, out, dst, slot, px, s);
+    if (!out_on_device) {
+        st = host_copy(ctx, out, dst, slot, px, s);
+        if (st != VR_OK) return st;
+    }
+    if (pipe) {
+        ctx->pipe_ready = true;
+        ctx->pipe_stream = s;
+        ctx->pipe_seq = ctx->input_seq;
+    }
     return VR_OK;
 }
 

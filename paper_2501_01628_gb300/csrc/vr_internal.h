@@ -224,7 +224,9 @@ cudaError_t launch_pack(const PackParams &p, int kind, cudaStream_t s);
 // after_composite: launch as a programmatic dependent of the preceding kernel
 // (the previous pipelined frame's composite); see march_kernel.
 cudaError_t launch_march(const MarchParams &p, int kind, cudaStream_t s, bool after_composite = false);
-cudaError_t launch_march_cycle(const MarchParams &p, int kind, float4 *out, cudaStream_t s);
+// after_frame: launch as a programmatic dependent of the preceding kernel (the
+// previous pipelined frame); see march_cycle_kernel.
+cudaError_t launch_march_cycle(const MarchParams &p, int kind, float4 *out, cudaStream_t s, bool after_frame = false);
 // max_blocks > 0: a grid of at most that many blocks, each compositing tiles in
 // turn; 0: one block per tile.
 cudaError_t launch_composite(const CompositeParams &p, cudaStream_t s, int max_blocks = 0);

@@ -134,6 +134,10 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
 template <typename S, bool COUNT, bool OPC>
 __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant__ MarchParams p, float4 *out)
 {
+    // pipelined frames: the next frame's kernel may start once every block of
+    // this grid is running, and this grid's image store waits for the
+    // preceding grid (see march_kernel); outside such launches both are no-ops
+    asm volatile("griddepcontrol.launch_dependents;");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = blockIdx.x * p.tile_w + (warp & 1) * p.pw + (lane & (p.pw - 1));
     const int py = blockIdx.y * p.tile_h + (warp >> 1) * (32 / p.pw) + lane / p.pw;
@@ -152,6 +156,7 @@ __global__ void __launch_bounds__(128) march_cycle_kernel(const __grid_constant_
                                              C2, T, executed, p.opc_ratio, p.count_error);
         if (T <= p.ert_T) break;
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     out[static_cast<long long>(py) * p.W + px] = make_float4(C0, C1, C2, 1.0f - T);
     if (COUNT && executed) atomicAdd(p.sample_counter, executed);
 }
@@ -208,27 +213,37 @@ cudaError_t launch_march(const MarchParams &p, int kind, cudaStream_t s, bool af
     return e;
 }
 
-cudaError_t launch_march_cycle(const MarchParams &p, int kind, float4 *out, cudaStream_t s)
+cudaError_t launch_march_cycle(const MarchParams &p, int kind, float4 *out, cudaStream_t s, bool after_frame)
 {
     if (p.W <= 0 || p.H <= 0) return cudaSuccess;
     const dim3 grid((p.W + p.tile_w - 1) / p.tile_w, (p.H + p.tile_h - 1) / p.tile_h);
     const bool count = p.sample_counter != nullptr;
     const bool opc = p.opc_ratio != 1.0f;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_frame ? 1 : 0;
 #define VR_CYCLE(T)                                                                                    \
-    (opc ? (count ? (march_cycle_kernel<T, true, true><<<grid, 128, 0, s>>>(p, out), 0)                \
-                  : (march_cycle_kernel<T, false, true><<<grid, 128, 0, s>>>(p, out), 0))              \
-         : (count ? (march_cycle_kernel<T, true, false><<<grid, 128, 0, s>>>(p, out), 0)               \
-                  : (march_cycle_kernel<T, false, false><<<grid, 128, 0, s>>>(p, out), 0)))
+    (opc ? (count ? cudaLaunchKernelEx(&cfg, march_cycle_kernel<T, true, true>, p, out)                \
+                  : cudaLaunchKernelEx(&cfg, march_cycle_kernel<T, false, true>, p, out))              \
+         : (count ? cudaLaunchKernelEx(&cfg, march_cycle_kernel<T, true, false>, p, out)               \
+                  : cudaLaunchKernelEx(&cfg, march_cycle_kernel<T, false, false>, p, out)))
+    cudaError_t e = cudaErrorInvalidValue;
     switch (kind) {
-    case kStoreF32: VR_CYCLE(float); break;
-    case kStoreBF16: VR_CYCLE(__nv_bfloat16); break;
-    case kStoreF16: VR_CYCLE(__half); break;
-    case kStoreBF16Oct: VR_CYCLE(dev::Octet<__nv_bfloat16>); break;
-    case kStoreF16Oct: VR_CYCLE(dev::Octet<__half>); break;
+    case kStoreF32: e = VR_CYCLE(float); break;
+    case kStoreBF16: e = VR_CYCLE(__nv_bfloat16); break;
+    case kStoreF16: e = VR_CYCLE(__half); break;
+    case kStoreBF16Oct: e = VR_CYCLE(dev::Octet<__nv_bfloat16>); break;
+    case kStoreF16Oct: e = VR_CYCLE(dev::Octet<__half>); break;
     default: return cudaErrorInvalidValue;
     }
 #undef VR_CYCLE
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace vr

@@ -263,3 +263,30 @@ def test_pipelined_asynchronous_host_outputs(vr):
     finally:
         _close(vr, ctx, v)
     _assert_equal(want, hosts)
+
+
+def test_pipelined_cycling_and_mixed_modes(vr):
+    """Ray-state cycling frames (mode 1) pipelined, alone and alternating with
+    sort-last frames, equal the plain sequence bit for bit."""
+    vol, tf, rng = _scene(seed=23)
+    part = dict(kind="kd", n_bricks=8, cut_fracs=rng.uniform(0.3, 0.7, 7))
+    cams = [synth.orbit_camera(97, 63, az, elevation_deg=el) for az, el in ((5, 20), (95, -15), (185, 40), (275, 0))]
+    modes = [1, 1, 1, 0, 1, 0, 0, 1]
+    res = {}
+    for pipelined in (False, True):
+        ctx, v = _ctx(vr, vol, part, tf, pipelined, schedule=(2, 4), ert=0.97)
+        try:
+            import torch
+            outs = []
+            for i, m in enumerate(modes):
+                vr.vr_set_render_mode(ctx, m)
+                cam = cams[i % len(cams)]
+                vr.vr_set_camera(ctx, cam)
+                o = torch.full((cam["height"], cam["width"], 4), float("nan"), device="cuda")
+                vr.vr_render_frame(ctx, v, o)
+                outs.append(o)
+            vr.vr_sync(ctx)
+            res[pipelined] = [o.cpu() for o in outs]
+        finally:
+            _close(vr, ctx, v)
+    _assert_equal(res[False], res[True])
