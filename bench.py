@@ -53,6 +53,8 @@ def args_parse():
     ap.add_argument("--workload", default="paper",
                     choices=["paper", "small", "precision", "grad", "batch", "stream", "mesh"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--layout", default="quads", choices=["quads", "octets"],
+                    help="batch workload: 16-bit cells as xy-quads or as octets (vr_set_cell_layout)")
     ap.add_argument("--split", default="views", choices=["views", "bricks"],
                     help="multi-GPU: replicas over views (weak scaling) or bricks as ranks with a radix-k "
                          "image exchange (strong scaling)")
@@ -779,6 +781,7 @@ def run_batch(a):
     cams = [synth.orbit_camera(1024, 1024, 360.0 * w / nviews, elevation_deg=20.0 * np.cos(w))
             for w in range(nviews)]
     ctx = vr.vr_create(0)
+    vr.vr_set_cell_layout(ctx, 1 if a.layout == "octets" else 0)
     vols, ranges = [], []
     for st in range(steps):
         for f in range(nfields):
@@ -838,6 +841,7 @@ def run_batch(a):
                 config=dict(workload="batching: 6 steps x 3 fields x 768^3 f16 (seed 3), 48 kd bricks, 32 views at "
                                      "1024x1024 = 576 renders + compositing in one persistent CUDA-graph launch"),
                 renders_per_s=nr / (batch_ms / 1e3), samples_per_batch=samples, storage_bytes=storage,
+                cell_layout=a.layout,
                 autotune=dict(packet_width=chosen[0], blocks_per_sm=chosen[1], ring_slots=chosen[2],
                               order="brick-major per volume" if chosen[3] == 1 else "render-major",
                               seconds=tune_s),
