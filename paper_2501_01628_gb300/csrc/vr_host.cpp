@@ -695,9 +695,10 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
 }
 
 // A sort-last frame into the caller's image. Pipelined frames (device output
-// or asynchronous host output, kernel timing off, the quad march) alternate between the context's two
-// frames and composite with a persistent grid of two blocks per multiprocessor,
-// which is resident early in the march's tail; its blocks signal at their start,
+// or asynchronous host output, kernel timing off, the quad march) alternate
+// between the context's two frames and composite with a persistent grid of two
+// blocks per multiprocessor, which is resident early in the march's tail; its
+// blocks signal at their start,
 // so the next frame's march (launched as a programmatic dependent when nothing
 // it reads before its waits has changed, on the same stream) can fill the
 // multiprocessors as this frame's march drains. Every write of that march waits
