@@ -17,7 +17,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
-SOURCES = ["vr_kernels.cu", "vr_composite.cu", "vr_host.cpp", "vr_noalloc.cu", "vr_grad.cu", "vr_batch.cu", "vr_mesh.cu",
+SOURCES = ["vr_kernels.cu", "vr_composite.cu", "vr_cycle.cu", "vr_host.cpp", "vr_noalloc.cu", "vr_grad.cu", "vr_batch.cu", "vr_mesh.cu",
            "vr_mesh_host.cpp", "vr_staged.cu"]
 
 
