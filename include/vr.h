@@ -190,11 +190,13 @@ vr_status vr_set_composite_schedule(vr_ctx ctx, int n_factors, const int *factor
 vr_status vr_set_opacity_correction(vr_ctx ctx, float ref_step_voxels);
 /* Host outputs (out_on_device == 0 in vr_composite / vr_render_frame) are
  * synchronous by default: the call returns with the image in host memory. With
- * on != 0 the call returns at once; the image is copied from one of two device
- * staging buffers on the context's own copy stream, overlapping the next
- * frame's rendering, and is in host memory after vr_sync(ctx, stream). Use
- * pinned host buffers, and a different host buffer for each of two consecutive
- * frames. */
+ * on != 0 the call returns without waiting for its own image; the image is
+ * copied from one of two device staging buffers on the context's own copy
+ * stream, overlapping the next frame's rendering, and is in host memory after
+ * vr_sync(ctx, stream). A call first waits on the host until the staging
+ * buffer's previous copy (two calls back) is done (inside stream capture the
+ * stream waits instead). Use pinned host buffers, and a different host buffer
+ * for each of two consecutive frames. */
 vr_status vr_set_host_output_async(vr_ctx ctx, int on);
 /* Ray-packet shape of the march: each warp marches packet_width x
  * (32/packet_width) neighbouring pixels (4, 8 or 16; default 4). The image does

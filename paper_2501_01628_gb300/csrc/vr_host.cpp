@@ -622,7 +622,17 @@ vr_status host_staging(vr_ctx ctx, long long px, cudaStream_t s, float4 **buf, i
     }
     const int k = ctx->img_next;
     ctx->img_next ^= 1;
-    VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_copied[k], 0));
+    // The staging image is free once its previous copy (two frames back) is
+    // done. Outside stream capture the host waits for that here, which keeps
+    // the render stream free of wait nodes: a wait between a pipelined frame's
+    // march and its composite would keep the composite from becoming resident
+    // in the march's tail (and the next march from starting there).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    VR_CUDA(ctx, cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone)
+        VR_CUDA(ctx, cudaEventSynchronize(ctx->ev_copied[k]));
+    else
+        VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_copied[k], 0));
     *buf = ctx->d_img2[k];
     *slot = k;
     return VR_OK;
