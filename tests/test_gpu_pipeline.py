@@ -290,3 +290,39 @@ def test_pipelined_cycling_and_mixed_modes(vr):
         finally:
             _close(vr, ctx, v)
     _assert_equal(res[False], res[True])
+
+
+def test_pipelined_frames_with_kernel_timing_and_toggles(vr):
+    """Kernel timing switched on and off, pipelining switched off and on, and
+    the maximum of 128 bricks, all inside one sequence: every frame equals the
+    plain sequence's."""
+    import torch
+    vol, tf, rng = _scene(n=64, seed=29)
+    part = dict(kind="grid", grid=(8, 4, 4))  # 128 bricks
+    cams = [synth.orbit_camera(120, 80, az, elevation_deg=el) for az, el in ((15, 20), (135, -25), (255, 45))]
+    plan = [("frame", 0), ("frame", 1), ("timing", True), ("frame", 2), ("frame", 0), ("timing", False),
+            ("frame", 1), ("pipe", False), ("frame", 2), ("pipe", True), ("frame", 0), ("frame", 1)]
+    res = {}
+    for pipelined in (False, True):
+        ctx, v = _ctx(vr, vol, part, tf, pipelined, schedule=(2, 4, 4, 4), ert=0.99)
+        try:
+            outs = []
+            for op, arg in plan:
+                if op == "timing":
+                    vr.vr_set_kernel_timing(ctx, arg)
+                    if not arg:
+                        t = vr.vr_get_kernel_timing(ctx)
+                        assert t["march_launches"] == 2 and t["composite_launches"] == 2
+                elif op == "pipe":
+                    vr.vr_set_frame_pipelining(ctx, arg and pipelined)
+                else:
+                    cam = cams[arg]
+                    vr.vr_set_camera(ctx, cam)
+                    o = torch.full((cam["height"], cam["width"], 4), float("nan"), device="cuda")
+                    vr.vr_render_frame(ctx, v, o)
+                    outs.append(o)
+            vr.vr_sync(ctx)
+            res[pipelined] = [o.cpu() for o in outs]
+        finally:
+            _close(vr, ctx, v)
+    _assert_equal(res[False], res[True])
