@@ -231,9 +231,9 @@ vr_status vr_set_march_staging(vr_ctx ctx, int on);
  * came in between. Images are bit-identical either way. Kernel timing,
  * synchronous host outputs and the staged march use the plain sequence (one
  * frame, one block per composite tile). Costs a second partial pool per
- * context. Ray-state cycling frames (vr_set_render_mode 1) are pipelined the
- * same way: the next frame's kernel may start while this one drains, and
- * writes its image after this one completes. */
+ * context. Ray-state cycling frames (vr_set_render_mode 1) and mesh frames
+ * (vr_render_mesh_frame) are pipelined the same way: the next frame's kernel
+ * may start while this one drains, and writes after this one completes. */
 vr_status vr_set_frame_pipelining(vr_ctx ctx, int on);
 /* Cell layout of bfloat16 / float16 volumes created afterwards (the precision
  * form: 16-bit storage, float32 arithmetic). 0 (default): xy-quads, four

@@ -669,6 +669,46 @@ vr_status composite_to(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device
     return host_copy(ctx, out, buf, slot, px, s);
 }
 
+// Pipelined frames: whether this frame's first kernel may be launched as a
+// programmatic dependent of the preceding kernel -- the previous pipelined
+// frame was launched on the same stream and no brick pack or table upload of
+// this context came since (input_seq). Until this frame's last kernel is
+// launched (pipe_launched) no further frame may overlap.
+bool pipe_after(vr_ctx ctx, cudaStream_t s)
+{
+    const bool after = ctx->pipe_ready && ctx->pipe_stream == s && ctx->pipe_seq == ctx->input_seq;
+    ctx->pipe_ready = false;
+    return after;
+}
+
+void pipe_launched(vr_ctx ctx, cudaStream_t s)
+{
+    ctx->pipe_ready = true;
+    ctx->pipe_stream = s;
+    ctx->pipe_seq = ctx->input_seq;
+}
+
+bool pipelined_output(vr_ctx ctx, int out_on_device)
+{
+    return ctx->pipelining && (out_on_device || ctx->host_async) && !ctx->timing;
+}
+
+// The composite of a pipelined frame: a persistent grid of two blocks per
+// multiprocessor, into the caller's device image or into one of the two
+// staging images copied on the copy stream.
+vr_status composite_pipelined(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s)
+{
+    const int blocks = ctx->sms > 0 ? 2 * ctx->sms : 0;
+    if (out_on_device) return composite(ctx, fr, reinterpret_cast<float4 *>(out), s, blocks);
+    const long long px = static_cast<long long>(fr.W) * fr.H;
+    float4 *buf = nullptr;
+    int slot = -1;
+    vr_status st = host_staging(ctx, px, s, &buf, &slot);
+    if (st == VR_OK) st = composite(ctx, fr, buf, s, blocks);
+    if (st == VR_OK) st = host_copy(ctx, out, buf, slot, px, s);
+    return st;
+}
+
 // Ray-state cycling frame straight into the image (device or host output).
 vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cudaStream_t s)
 {
@@ -686,9 +726,8 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
     // pipelined frames (see render_to): this frame's kernel may start in the
     // previous frame's tail; it reads only the bricks and the table before it
     // waits, and writes its image after the preceding grid completes
-    const bool pipe = ctx->pipelining && (out_on_device || ctx->host_async) && !ctx->timing;
-    const bool after = pipe && ctx->pipe_ready && ctx->pipe_stream == s && ctx->pipe_seq == ctx->input_seq;
-    ctx->pipe_ready = false;
+    const bool pipe = pipelined_output(ctx, out_on_device);
+    const bool after = pipe_after(ctx, s) && pipe;
     const int t = timing_begin(ctx, 0, s);
     VR_LAUNCH(ctx, launch_march_cycle(mp, vol->kind(), dst, s, after));
     timing_end(ctx, t, s);
@@ -696,11 +735,7 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
         st = host_copy(ctx, out, dst, slot, px, s);
         if (st != VR_OK) return st;
     }
-    if (pipe) {
-        ctx->pipe_ready = true;
-        ctx->pipe_stream = s;
-        ctx->pipe_seq = ctx->input_seq;
-    }
+    if (pipe) pipe_launched(ctx, s);
     return VR_OK;
 }
 
@@ -717,8 +752,7 @@ vr_status cycle_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cud
 vr_status render_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cudaStream_t s)
 {
     if (!out) return fail(ctx, VR_ERR_ARG, "null output");
-    const bool pipe = ctx->pipelining && (out_on_device || ctx->host_async) && !ctx->timing &&
-                      !(ctx->staging && vol->d_scalar);
+    const bool pipe = pipelined_output(ctx, out_on_device) && !(ctx->staging && vol->d_scalar);
     if (!pipe) {
         ctx->pipe_ready = false;
         vr_status st = march(ctx, vol, ctx->frame, s);
@@ -726,25 +760,11 @@ vr_status render_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cu
         return composite_to(ctx, ctx->frame, out, out_on_device, s);
     }
     vr_frame_s &fr = ctx->frame_next ? ctx->frame2 : ctx->frame;
-    const bool after = ctx->pipe_ready && ctx->pipe_stream == s && ctx->pipe_seq == ctx->input_seq;
-    ctx->pipe_ready = false;  // until this frame's composite is launched
-    vr_status st = march(ctx, vol, fr, s, after);
+    vr_status st = march(ctx, vol, fr, s, pipe_after(ctx, s));
     if (st != VR_OK) return st;
-    const int blocks = ctx->sms > 0 ? 2 * ctx->sms : 0;
-    if (out_on_device) {
-        st = composite(ctx, fr, reinterpret_cast<float4 *>(out), s, blocks);
-    } else {  // one of the two staging images, copied on the copy stream
-        const long long px = static_cast<long long>(fr.W) * fr.H;
-        float4 *buf = nullptr;
-        int slot = -1;
-        st = host_staging(ctx, px, s, &buf, &slot);
-        if (st == VR_OK) st = composite(ctx, fr, buf, s, blocks);
-        if (st == VR_OK) st = host_copy(ctx, out, buf, slot, px, s);
-    }
+    st = composite_pipelined(ctx, fr, out, out_on_device, s);
     if (st != VR_OK) return st;
-    ctx->pipe_ready = true;
-    ctx->pipe_stream = s;
-    ctx->pipe_seq = ctx->input_seq;
+    pipe_launched(ctx, s);
     ctx->frame_next ^= 1;
     return VR_OK;
 }

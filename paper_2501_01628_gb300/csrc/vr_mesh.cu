@@ -69,12 +69,26 @@ __device__ int locate(const MeshParams &p, int brick, float qx, float qy, float 
     return best;
 }
 
-// 8 blocks of 128 threads per SM: at most 64 registers per thread
+// 8 blocks of 128 threads per SM: at most 64 registers per thread; a mask block
+// writes one tile mask per thread
+static_assert(kMaskThreads == 128, "mask blocks are march blocks");
 template <bool COUNT, bool OPC>
 __global__ void __launch_bounds__(128, 8) march_mesh_kernel(const __grid_constant__ MeshParams P)
 {
     const MarchParams &p = P.m;
-    const int item = blockIdx.x;
+    // pipelined frames: the next grid may start once every block of this one
+    // is running, and this grid writes (masks, partials) only after the
+    // preceding grid completes; outside such launches the wait returns at once
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (static_cast<int>(blockIdx.x) < p.mask_blocks) {  // the composite's tile masks
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        dev::write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.mask_tiles_x, p.mask_tiles_y, p.nb, p.order,
+                             [&](int b) { return make_int4(p.b[b].rect[0], p.b[b].rect[1], p.b[b].rect[2],
+                                                           p.b[b].rect[3]); },
+                             p.tile_mask);
+        return;
+    }
+    const int item = blockIdx.x - p.mask_blocks;
     const int bi = find_brick(p, item);
     const BrickLaunch &B = p.b[bi];
     const int local = item - B.item_begin;
@@ -196,24 +210,31 @@ __global__ void __launch_bounds__(128, 8) march_mesh_kernel(const __grid_constan
             nb = pn;
         }
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = make_float4(C0, C1, C2, 1.0f - T);
     if (COUNT && executed) atomicAdd(p.sample_counter, executed);
 }
 
 }  // namespace
 
-cudaError_t launch_march_mesh(const MeshParams &p, cudaStream_t s)
+cudaError_t launch_march_mesh(const MeshParams &p, cudaStream_t s, bool after_frame)
 {
-    if (p.m.n_items <= 0) return cudaSuccess;
+    const int grid = p.m.n_items + p.m.mask_blocks;
+    if (grid <= 0) return cudaSuccess;
     const bool count = p.m.sample_counter != nullptr, opc = p.m.opc_ratio != 1.0f;
-    if (count) {
-        if (opc) march_mesh_kernel<true, true><<<p.m.n_items, 128, 0, s>>>(p);
-        else march_mesh_kernel<true, false><<<p.m.n_items, 128, 0, s>>>(p);
-    } else {
-        if (opc) march_mesh_kernel<false, true><<<p.m.n_items, 128, 0, s>>>(p);
-        else march_mesh_kernel<false, false><<<p.m.n_items, 128, 0, s>>>(p);
-    }
-    return cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_frame ? 1 : 0;
+    if (count) return opc ? cudaLaunchKernelEx(&cfg, march_mesh_kernel<true, true>, p)
+                          : cudaLaunchKernelEx(&cfg, march_mesh_kernel<true, false>, p);
+    return opc ? cudaLaunchKernelEx(&cfg, march_mesh_kernel<false, true>, p)
+               : cudaLaunchKernelEx(&cfg, march_mesh_kernel<false, false>, p);
 }
 
 }  // namespace vr

@@ -50,6 +50,9 @@ struct MeshParams {
     int *error;                       // bit 3: a point location found no element (empty brick)
 };
 
-cudaError_t launch_march_mesh(const MeshParams &p, cudaStream_t s);
+// The grid starts with p.m.mask_blocks blocks that write the composite's tile
+// masks. after_frame: launch as a programmatic dependent of the preceding
+// kernel (the previous pipelined frame).
+cudaError_t launch_march_mesh(const MeshParams &p, cudaStream_t s, bool after_frame = false);
 
 }  // namespace vr

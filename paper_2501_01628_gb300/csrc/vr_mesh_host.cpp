@@ -364,6 +364,7 @@ vr_status vr_mesh_create(vr_ctx ctx, const int dims[3], const vr_partition *part
     }
     m->bytes = static_cast<long long>(rec_bytes + nbr_bytes + node_bytes);
     ctx->live_objects++;
+    ctx->input_seq++;  // new device data a pipelined kernel must not overlap
     *out = m.release();
     return VR_OK;
 }
@@ -400,11 +401,20 @@ vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int ou
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     static thread_local MeshParams mp;  // ~15 KB: keep off the stack
-    vr_status st = prepare_frame(ctx, &mesh->geom, ctx->frame, mp.m);
+    // pipelined frames as for volumes (vr_set_frame_pipelining)
+    const bool pipe = vr::host::pipelined_output(ctx, out_on_device);
+    vr_frame_s &fr = pipe && ctx->frame_next ? ctx->frame2 : ctx->frame;
+    const bool after = vr::host::pipe_after(ctx, s) && pipe;
+    vr_status st = prepare_frame(ctx, &mesh->geom, fr, mp.m);
     if (st != VR_OK) return st;
-    st = ensure_frame(ctx, ctx->frame, std::max(ctx->frame.pool_px, 1LL));
+    st = ensure_frame(ctx, fr, std::max(fr.pool_px, 1LL));
     if (st != VR_OK) return st;
-    mp.m.partials = ctx->frame.d_part;
+    mp.m.partials = fr.d_part;
+    // the grid's first blocks write the composite's tile masks
+    mp.m.tile_mask = reinterpret_cast<uint4 *>(fr.d_part + fr.total_px);
+    mp.m.mask_tiles_x = fr.tiles_x;
+    mp.m.mask_tiles_y = fr.tiles_y;
+    mp.m.mask_blocks = (fr.tiles_x * fr.tiles_y + kMaskThreads - 1) / kMaskThreads;
     mp.rec = mesh->d_rec;
     mp.nbr = mesh->d_nbr;
     mp.nodes = mesh->d_nodes;
@@ -414,9 +424,15 @@ vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int ou
     }
     mp.error = ctx->d_error;
     const int t = timing_begin(ctx, 0, s);
-    VR_LAUNCH(ctx, launch_march_mesh(mp, s));
+    VR_LAUNCH(ctx, launch_march_mesh(mp, s, after));
     timing_end(ctx, t, s);
-    return composite_to(ctx, ctx->frame, out_rgba, out_on_device, s);
+    fr.masks_ready = true;
+    if (!pipe) return composite_to(ctx, fr, out_rgba, out_on_device, s);
+    st = vr::host::composite_pipelined(ctx, fr, out_rgba, out_on_device, s);
+    if (st != VR_OK) return st;
+    vr::host::pipe_launched(ctx, s);
+    ctx->frame_next ^= 1;
+    return VR_OK;
 }
 
 }  // extern "C"

@@ -183,6 +183,11 @@ bool partition_plan(const int dims[3], const vr_partition *part, std::vector<int
 vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &mp);
 vr_status ensure_frame(vr_ctx ctx, vr_frame_s &fr, long long px);
 vr_status composite_to(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s);
+// pipelined frames (vr_set_frame_pipelining; vr_host.cpp)
+bool pipelined_output(vr_ctx ctx, int out_on_device);
+bool pipe_after(vr_ctx ctx, cudaStream_t s);
+void pipe_launched(vr_ctx ctx, cudaStream_t s);
+vr_status composite_pipelined(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s);
 int timing_begin(vr_ctx ctx, int kind, cudaStream_t s);
 void timing_end(vr_ctx ctx, int idx, cudaStream_t s);
 

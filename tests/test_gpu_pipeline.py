@@ -326,3 +326,53 @@ def test_pipelined_frames_with_kernel_timing_and_toggles(vr):
         finally:
             _close(vr, ctx, v)
     _assert_equal(res[False], res[True])
+
+
+def test_pipelined_mesh_frames(vr):
+    """Tetrahedral-mesh frames pipelined (the mesh march writes the tile masks,
+    starts in the previous frame's tail and writes after it), alternating with
+    voxel frames of the same context: every image equals the plain sequence's,
+    and the mesh images equal a fresh plain render."""
+    import torch
+    n = 32
+    part = dict(kind="kd", n_bricks=6, cut_fracs=np.linspace(0.35, 0.65, 5))
+    boxes = vr.vr_partition_boxes((n, n, n), part)
+    rng = np.random.default_rng(31)
+    verts, tets = synth.tet_mesh((n, n, n), boxes, rng, cell_voxels=3.0, jitter=0.2, refine=1.5,
+                                 focus=(0.35, 0.6, 0.45))
+    vals = synth.mesh_field(rng, verts)
+    tf = synth.random_tf(rng, alpha_max=0.04)
+    lo, hi = float(vals.min()), float(vals.max())
+    vol = synth.blob_volume(n, synth.draw_blobs(rng, 5))
+    cams = [synth.orbit_camera(90, 66, az, elevation_deg=el) for az, el in ((10, 20), (130, -30), (250, 50))]
+    plan = ["mesh", "mesh", "vol", "mesh", "mesh", "vol", "vol", "mesh"]
+    res = {}
+    for pipelined in (False, True):
+        ctx = vr.vr_create(0)
+        m = v = None
+        try:
+            vr.vr_set_frame_pipelining(ctx, pipelined)
+            m = vr.vr_mesh_create(ctx, verts, vals, tets, (n, n, n), part)
+            v = vr.vr_volume_create(ctx, vol, "f32", part)
+            vr.vr_set_transfer_function(ctx, tf, lo, hi)
+            vr.vr_set_render_params(ctx, 0.5, 0.99)
+            vr.vr_set_composite_schedule(ctx, (2, 3))
+            outs = []
+            for i, kind in enumerate(plan):
+                cam = cams[i % len(cams)]
+                vr.vr_set_camera(ctx, cam)
+                o = torch.full((cam["height"], cam["width"], 4), float("nan"), device="cuda")
+                if kind == "mesh":
+                    vr.vr_render_mesh_frame(ctx, m, o)
+                else:
+                    vr.vr_render_frame(ctx, v, o)
+                outs.append(o)
+            vr.vr_sync(ctx)
+            res[pipelined] = [o.cpu() for o in outs]
+        finally:
+            if m is not None:
+                vr.vr_mesh_release(m)
+            if v is not None:
+                vr.vr_volume_release(v)
+            vr.vr_destroy(ctx)
+    _assert_equal(res[False], res[True])
