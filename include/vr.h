@@ -224,16 +224,20 @@ vr_status vr_set_march_staging(vr_ctx ctx, int on);
  * can start while this frame's march drains and its composite runs
  * (programmatic dependent launch; Sec. 3's render-then-composite per frame,
  * overlapped between consecutive frames). Ordering stays that of the stream:
- * every write of the overlapping march (its partials and tile masks) waits for
- * the previous composite to complete, and the march overlaps only when the
- * previous pipelined frame was launched on the same stream and no brick pack
- * (volume create or update) and no transfer-function upload of this context
+ * the overlapping march's tile masks wait for the previous composite to
+ * complete (so the march completes only after it), its partials wait only for
+ * the composite that last read their pool (two frames back; a bounded wait on
+ * a device flag that composite releases -- if it gives up, the next vr_sync
+ * returns VR_ERR_TIMEOUT and the frame's partials are not written), and the
+ * march overlaps only when the previous pipelined frame was launched on the
+ * same stream and no brick pack (volume create or update) and no
+ * transfer-function upload of this context
  * came in between. Images are bit-identical either way. Kernel timing,
  * synchronous host outputs and the staged march use the plain sequence (one
  * frame, one block per composite tile). Costs a second partial pool per
- * context. Ray-state cycling frames (vr_set_render_mode 1) and mesh frames
- * (vr_render_mesh_frame) are pipelined the same way: the next frame's kernel
- * may start while this one drains, and writes after this one completes. */
+ * context. Mesh frames (vr_render_mesh_frame) are pipelined the same way;
+ * ray-state cycling frames (vr_set_render_mode 1) too, their kernel writing
+ * its image after the previous frame's last kernel completes. */
 vr_status vr_set_frame_pipelining(vr_ctx ctx, int on);
 /* Cell layout of bfloat16 / float16 volumes created afterwards (the precision
  * form: 16-bit storage, float32 arithmetic). 0 (default): xy-quads, four

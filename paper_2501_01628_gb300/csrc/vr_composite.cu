@@ -136,6 +136,19 @@ __global__ void __launch_bounds__(256) composite_kernel(const __grid_constant__ 
         }
     }
     }
+    if (p.pool_done) {
+        // pipelined frames: once every block has read its partials, the last
+        // block to finish releases the pool to the frame after next
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            __threadfence();
+            if (atomicAdd(p.pool_count + p.pool, 1u) == gridDim.x - 1) {
+                p.pool_count[p.pool] = 0;  // for the pool's next composite
+                asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p.pool_done + p.pool), "l"(p.pool_frame)
+                             : "memory");
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -510,7 +510,8 @@ void timing_end(vr_ctx ctx, int idx, cudaStream_t s)
     if (idx >= 0) cudaEventRecord(ctx->timed[idx].b, s);
 }
 
-vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s, bool after_composite = false)
+vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s, bool after_composite = false,
+                const PoolSync *sync = nullptr)
 {
     static thread_local MarchParams mp;  // ~12 KB: keep off the stack
     vr_status st = prepare_frame(ctx, vol, fr, mp);
@@ -523,6 +524,11 @@ vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s, bool 
     mp.mask_tiles_x = fr.tiles_x;
     mp.mask_tiles_y = fr.tiles_y;
     mp.mask_blocks = (fr.tiles_x * fr.tiles_y + kMaskThreads - 1) / kMaskThreads;
+    if (sync) {
+        mp.pool_done = sync->done;
+        mp.pool_frame = sync->frame;
+        mp.pool = sync->pool;
+    }
     const int t = timing_begin(ctx, 0, s);
     if (ctx->staging && vol->d_scalar) {
         static thread_local StagedBricks sb;
@@ -540,7 +546,8 @@ vr_status march(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, cudaStream_t s, bool 
     return VR_OK;
 }
 
-vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s, int max_blocks = 0)
+vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s, int max_blocks = 0,
+                    const PoolSync *sync = nullptr)
 {
     static thread_local CompositeParams cp;
     std::memset(&cp, 0, sizeof(cp));
@@ -580,6 +587,12 @@ vr_status composite(vr_ctx ctx, vr_frame_s &fr, float4 *out, cudaStream_t s, int
         fr.masks_ready = true;
     }
     const int t = timing_begin(ctx, 1, s);
+    if (sync) {
+        cp.pool_done = sync->done;
+        cp.pool_count = sync->count;
+        cp.pool_frame = sync->frame;
+        cp.pool = sync->pool;
+    }
     VR_LAUNCH(ctx, launch_composite(cp, s, max_blocks));
     timing_end(ctx, t, s);
     return VR_OK;
@@ -693,20 +706,44 @@ bool pipelined_output(vr_ctx ctx, int out_on_device)
     return ctx->pipelining && (out_on_device || ctx->host_async) && !ctx->timing;
 }
 
+// The next pipelined frame's number and pool (frame n uses pool n % 2; its
+// march waits for the composite of frame n - 2, which read the same pool).
+PoolSync pipe_frame(vr_ctx ctx)
+{
+    const unsigned long long n = ++ctx->pool_frame;
+    return PoolSync{ctx->d_pool_done, ctx->d_pool_count, n, static_cast<int>(n & 1)};
+}
+
+vr_frame_s &pipe_pool(vr_ctx ctx, const PoolSync &sync)
+{
+    return sync.pool ? ctx->frame2 : ctx->frame;
+}
+
 // The composite of a pipelined frame: a persistent grid of two blocks per
 // multiprocessor, into the caller's device image or into one of the two
-// staging images copied on the copy stream.
-vr_status composite_pipelined(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s)
+// staging images copied on the copy stream; it releases the frame's pool when
+// done. A frame whose composite was not launched gives its number back, so the
+// pool's next march does not wait for a release that never comes.
+vr_status composite_pipelined(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s,
+                              const PoolSync &sync)
 {
     const int blocks = ctx->sms > 0 ? 2 * ctx->sms : 0;
-    if (out_on_device) return composite(ctx, fr, reinterpret_cast<float4 *>(out), s, blocks);
+    vr_status st = VR_OK;
+    if (out_on_device) {
+        st = composite(ctx, fr, reinterpret_cast<float4 *>(out), s, blocks, &sync);
+        if (st != VR_OK) ctx->pool_frame = sync.frame - 1;
+        return st;
+    }
     const long long px = static_cast<long long>(fr.W) * fr.H;
     float4 *buf = nullptr;
     int slot = -1;
-    vr_status st = host_staging(ctx, px, s, &buf, &slot);
-    if (st == VR_OK) st = composite(ctx, fr, buf, s, blocks);
-    if (st == VR_OK) st = host_copy(ctx, out, buf, slot, px, s);
-    return st;
+    st = host_staging(ctx, px, s, &buf, &slot);
+    if (st == VR_OK) st = composite(ctx, fr, buf, s, blocks, &sync);
+    if (st != VR_OK) {
+        ctx->pool_frame = sync.frame - 1;
+        return st;
+    }
+    return host_copy(ctx, out, buf, slot, px, s);
 }
 
 // Ray-state cycling frame straight into the image (device or host output).
@@ -759,13 +796,16 @@ vr_status render_to(vr_ctx ctx, vr_volume vol, float *out, int out_on_device, cu
         if (st != VR_OK) return st;
         return composite_to(ctx, ctx->frame, out, out_on_device, s);
     }
-    vr_frame_s &fr = ctx->frame_next ? ctx->frame2 : ctx->frame;
-    vr_status st = march(ctx, vol, fr, s, pipe_after(ctx, s));
-    if (st != VR_OK) return st;
-    st = composite_pipelined(ctx, fr, out, out_on_device, s);
+    const PoolSync sync = pipe_frame(ctx);
+    vr_frame_s &fr = pipe_pool(ctx, sync);
+    vr_status st = march(ctx, vol, fr, s, pipe_after(ctx, s), &sync);
+    if (st != VR_OK) {
+        ctx->pool_frame = sync.frame - 1;
+        return st;
+    }
+    st = composite_pipelined(ctx, fr, out, out_on_device, s, sync);
     if (st != VR_OK) return st;
     pipe_launched(ctx, s);
-    ctx->frame_next ^= 1;
     return VR_OK;
 }
 
@@ -839,10 +879,16 @@ vr_status vr_create(int cuda_device, vr_ctx *out)
     DeviceGuard g(cuda_device);
     if (!g.ok || vr::host::dev_malloc(&ctx->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(ctx->d_counter, 0, sizeof(unsigned long long)) != cudaSuccess ||
-        vr::host::dev_malloc(&ctx->d_error, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_error, 0, sizeof(int)) != cudaSuccess) {
+        vr::host::dev_malloc(&ctx->d_error, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_error, 0, sizeof(int)) != cudaSuccess ||
+        vr::host::dev_malloc(&ctx->d_pool_done, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_pool_done, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        vr::host::dev_malloc(&ctx->d_pool_count, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(ctx->d_pool_count, 0, 2 * sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(ctx->d_counter);
         cudaFree(ctx->d_error);
+        cudaFree(ctx->d_pool_done);
+        cudaFree(ctx->d_pool_count);
         delete ctx;
         return VR_ERR_CUDA;
     }
@@ -868,6 +914,8 @@ vr_status vr_destroy(vr_ctx ctx)
     cudaFree(ctx->d_gpart);
     cudaFree(ctx->frame.d_part);
     cudaFree(ctx->frame2.d_part);
+    cudaFree(ctx->d_pool_done);
+    cudaFree(ctx->d_pool_count);
     cudaFree(ctx->d_img);
     if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
     for (int i = 0; i < 2; ++i) {
@@ -932,6 +980,7 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
         VR_CUDA(ctx, cudaMemset(ctx->d_error, 0, sizeof(int)));
         if (err & 2) return fail(ctx, VR_ERR_TIMEOUT, "a bounded device-side wait of the batched kernel gave up");
         if (err & 32) return fail(ctx, VR_ERR_TIMEOUT, "a bounded wait for a staged brick slab gave up");
+        if (err & 64) return fail(ctx, VR_ERR_TIMEOUT, "a pipelined frame's bounded wait for its partial pool gave up");
         if (err & 8) return fail(ctx, VR_ERR_BOUNDS, "a mesh point location found no element");
         if (err & 16)
             return fail(ctx, VR_ERR_BOUNDS, "a counted sample's cell fell outside its brick's storage or staged box");

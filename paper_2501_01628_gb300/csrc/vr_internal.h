@@ -85,6 +85,13 @@ struct MarchParams {
     // position j overlaps composite tile t (kCompW x kCompTileH pixels)
     uint4 *tile_mask;
     int mask_tiles_x, mask_tiles_y, mask_blocks;
+    // pipelined frames: the partial pool this frame writes was last read by the
+    // composite of frame pool_frame - 2, which sets pool_done[pool] to its own
+    // frame number when it is done; the march blocks wait for that (null: no
+    // wait) before storing their partials
+    const unsigned long long *pool_done;
+    unsigned long long pool_frame;
+    int pool;
     int nb;
     int n_items;        // march work items (the grid adds mask_blocks in front)
     int order[kMaxBricks];  // brick ids front to back (ray-state cycling)
@@ -104,6 +111,12 @@ struct CompositeParams {
     float4 *out;
     uint4 *tile_mask;                 // per tile: visibility positions of the bricks overlapping it
     int tiles_x, tiles_y;             // composite tiles per row / column (kCompW x kCompTileH)
+    // pipelined frames: the grid's last block to finish sets pool_done[pool] =
+    // pool_frame (pool_count counts finished blocks; null: nothing published)
+    unsigned long long *pool_done;
+    unsigned int *pool_count;
+    unsigned long long pool_frame;
+    int pool;
 };
 
 // Composite adjoint: the composite's layout plus the image gradient and the

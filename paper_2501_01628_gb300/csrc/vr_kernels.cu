@@ -86,9 +86,11 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
     asm volatile("griddepcontrol.launch_dependents;");
     // Launched as a programmatic dependent of the previous frame's composite
     // (pipelined frames), this grid reads only the bricks and the table before
-    // the waits below; its writes (masks, partials) go to a pool that the frame
-    // before the previous one read, and wait for the preceding grid's completion.
-    // Outside such a launch the waits return at once.
+    // it waits; its writes (masks, partials) go to a pool that the frame before
+    // the previous one read. The mask blocks wait for the preceding grid's
+    // completion (so this grid completes only after it); the march blocks wait
+    // only for the composite that last read their pool (pool_ready). Outside
+    // such a launch both waits return at once.
     if (static_cast<int>(blockIdx.x) < p.mask_blocks) {  // the composite's tile masks
         asm volatile("griddepcontrol.wait;" ::: "memory");
         dev::write_tile_mask(blockIdx.x * kMaskThreads + threadIdx.x, p.mask_tiles_x, p.mask_tiles_y, p.nb, p.order,
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Marc
                                       p.count_error);
     // the composite reads the partial next: keep it in L2 ahead of the streamed bricks
     float4 *dst = p.partials + B.poff + static_cast<long long>(ry) * B.rect[2] + rx;
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (!dev::pool_ready(p.pool_done, p.pool, p.pool_frame, p.count_error)) return;
     unsigned long long policy;
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
     asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "f"(c.x), "f"(c.y),

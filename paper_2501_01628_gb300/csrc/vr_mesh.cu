@@ -77,8 +77,10 @@ __global__ void __launch_bounds__(128, 8) march_mesh_kernel(const __grid_constan
 {
     const MarchParams &p = P.m;
     // pipelined frames: the next grid may start once every block of this one
-    // is running, and this grid writes (masks, partials) only after the
-    // preceding grid completes; outside such launches the wait returns at once
+    // is running; the mask blocks write only after the preceding grid
+    // completes, and the march blocks store their partials once the composite
+    // that last read their pool is done (as in march_kernel); outside such
+    // launches both waits return at once
     asm volatile("griddepcontrol.launch_dependents;");
     if (static_cast<int>(blockIdx.x) < p.mask_blocks) {  // the composite's tile masks
         asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(128, 8) march_mesh_kernel(const __grid_constan
             nb = pn;
         }
     }
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (!dev::pool_ready(p.pool_done, p.pool, p.pool_frame, P.error)) return;
     p.partials[B.poff + static_cast<long long>(ry) * B.rect[2] + rx] = make_float4(C0, C1, C2, 1.0f - T);
     if (COUNT && executed) atomicAdd(p.sample_counter, executed);
 }

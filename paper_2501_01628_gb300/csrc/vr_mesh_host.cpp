@@ -403,13 +403,24 @@ vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int ou
     static thread_local MeshParams mp;  // ~15 KB: keep off the stack
     // pipelined frames as for volumes (vr_set_frame_pipelining)
     const bool pipe = vr::host::pipelined_output(ctx, out_on_device);
-    vr_frame_s &fr = pipe && ctx->frame_next ? ctx->frame2 : ctx->frame;
     const bool after = vr::host::pipe_after(ctx, s) && pipe;
+    PoolSync sync{};
+    if (pipe) sync = vr::host::pipe_frame(ctx);
+    vr_frame_s &fr = pipe ? vr::host::pipe_pool(ctx, sync) : ctx->frame;
+    auto give_back = [&](vr_status e) {  // no composite will release this frame's pool
+        if (pipe) ctx->pool_frame = sync.frame - 1;
+        return e;
+    };
     vr_status st = prepare_frame(ctx, &mesh->geom, fr, mp.m);
-    if (st != VR_OK) return st;
+    if (st != VR_OK) return give_back(st);
     st = ensure_frame(ctx, fr, std::max(fr.pool_px, 1LL));
-    if (st != VR_OK) return st;
+    if (st != VR_OK) return give_back(st);
     mp.m.partials = fr.d_part;
+    if (pipe) {
+        mp.m.pool_done = sync.done;
+        mp.m.pool_frame = sync.frame;
+        mp.m.pool = sync.pool;
+    }
     // the grid's first blocks write the composite's tile masks
     mp.m.tile_mask = reinterpret_cast<uint4 *>(fr.d_part + fr.total_px);
     mp.m.mask_tiles_x = fr.tiles_x;
@@ -424,14 +435,17 @@ vr_status vr_render_mesh_frame(vr_ctx ctx, vr_mesh mesh, float *out_rgba, int ou
     }
     mp.error = ctx->d_error;
     const int t = timing_begin(ctx, 0, s);
-    VR_LAUNCH(ctx, launch_march_mesh(mp, s, after));
+    st = [&]() -> vr_status {
+        VR_LAUNCH(ctx, launch_march_mesh(mp, s, after));
+        return VR_OK;
+    }();
+    if (st != VR_OK) return give_back(st);
     timing_end(ctx, t, s);
     fr.masks_ready = true;
     if (!pipe) return composite_to(ctx, fr, out_rgba, out_on_device, s);
-    st = vr::host::composite_pipelined(ctx, fr, out_rgba, out_on_device, s);
+    st = vr::host::composite_pipelined(ctx, fr, out_rgba, out_on_device, s, sync);
     if (st != VR_OK) return st;
     vr::host::pipe_launched(ctx, s);
-    ctx->frame_next ^= 1;
     return VR_OK;
 }
 

@@ -107,12 +107,17 @@ struct vr_ctx_s {
     // on the same stream: input_seq counts brick packs and table uploads.
     bool pipelining = true;
     vr_frame_s frame2;
-    int frame_next = 0;
     int sms = 0;                   // multiprocessors of the device (persistent composite grid)
     unsigned long long input_seq = 0;
     bool pipe_ready = false;
     cudaStream_t pipe_stream = nullptr;
     unsigned long long pipe_seq = 0;
+    // per pool (frame, frame2): the last pipelined frame whose composite read it
+    // and is done, and that composite's count of finished blocks (device);
+    // pipelined frames are numbered from 1 and frame n uses pool n % 2
+    unsigned long long *d_pool_done = nullptr;
+    unsigned int *d_pool_count = nullptr;
+    unsigned long long pool_frame = 0;
     float4 *d_img = nullptr;       // staging for host outputs
     long long img_cap = 0;
     // asynchronous host output: two staging images, copies on their own stream
@@ -183,11 +188,21 @@ bool partition_plan(const int dims[3], const vr_partition *part, std::vector<int
 vr_status prepare_frame(vr_ctx ctx, vr_volume vol, vr_frame_s &fr, MarchParams &mp);
 vr_status ensure_frame(vr_ctx ctx, vr_frame_s &fr, long long px);
 vr_status composite_to(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s);
-// pipelined frames (vr_set_frame_pipelining; vr_host.cpp)
+// pipelined frames (vr_set_frame_pipelining; vr_host.cpp): the pool wait of
+// a frame's march and the release by its composite
+struct PoolSync {
+    unsigned long long *done;
+    unsigned int *count;
+    unsigned long long frame;
+    int pool;
+};
 bool pipelined_output(vr_ctx ctx, int out_on_device);
 bool pipe_after(vr_ctx ctx, cudaStream_t s);
 void pipe_launched(vr_ctx ctx, cudaStream_t s);
-vr_status composite_pipelined(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s);
+PoolSync pipe_frame(vr_ctx ctx);
+vr_frame_s &pipe_pool(vr_ctx ctx, const PoolSync &sync);
+vr_status composite_pipelined(vr_ctx ctx, vr_frame_s &fr, float *out, int out_on_device, cudaStream_t s,
+                              const PoolSync &sync);
 int timing_begin(vr_ctx ctx, int kind, cudaStream_t s);
 void timing_end(vr_ctx ctx, int idx, cudaStream_t s);
 
