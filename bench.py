@@ -904,6 +904,7 @@ def run_stream(a):
                     torch.cuda.synchronize()
         # the first two steps are resident at creation; time steps 0..7
         res[prefetch] = timed(run)
+        vr.vr_sync(ctx)  # raises if a bounded device-side wait gave up
         r.close()
     # upload + pack of one step alone
     v = vr.vr_volume_create(ctx, host[0], "f32", part)
