@@ -239,6 +239,13 @@ vr_status vr_set_march_staging(vr_ctx ctx, int on);
  * ray-state cycling frames (vr_set_render_mode 1) too, their kernel writing
  * its image after the previous frame's last kernel completes. */
 vr_status vr_set_frame_pipelining(vr_ctx ctx, int on);
+/* Test hook of the pipelined frames' bounded pool wait: advances the context's
+ * frame count by two without rendering, so the next pipelined frame's march
+ * waits for a pool release that never comes; after its bounded wait (2^20
+ * polls per thread) it skips its partials, and the next vr_sync returns
+ * VR_ERR_TIMEOUT and re-arms the pool flags, so the following frames render
+ * normally. Nothing faults or hangs. */
+vr_status vr_debug_pipeline_gap(vr_ctx ctx);
 /* Cell layout of bfloat16 / float16 volumes created afterwards (the precision
  * form: 16-bit storage, float32 arithmetic). 0 (default): xy-quads, four
  * voxels of one plane per 8-byte element, two loads per sample. 1: octets,

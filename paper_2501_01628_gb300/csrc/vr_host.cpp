@@ -978,6 +978,15 @@ vr_status vr_sync(vr_ctx ctx, void *stream)
     VR_CUDA(ctx, cudaMemcpy(&err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         VR_CUDA(ctx, cudaMemset(ctx->d_error, 0, sizeof(int)));
+        if (err & 64) {
+            // a pool wait gave up: once the device is idle, mark every pool as
+            // released up to the current frame, so later frames do not wait
+            VR_CUDA(ctx, cudaDeviceSynchronize());
+            const unsigned long long done[2] = {ctx->pool_frame, ctx->pool_frame};
+            VR_CUDA(ctx, cudaMemcpy(ctx->d_pool_done, done, sizeof(done), cudaMemcpyHostToDevice));
+            VR_CUDA(ctx, cudaMemset(ctx->d_pool_count, 0, 2 * sizeof(unsigned int)));
+            ctx->pipe_ready = false;
+        }
         if (err & 2) return fail(ctx, VR_ERR_TIMEOUT, "a bounded device-side wait of the batched kernel gave up");
         if (err & 32) return fail(ctx, VR_ERR_TIMEOUT, "a bounded wait for a staged brick slab gave up");
         if (err & 64) return fail(ctx, VR_ERR_TIMEOUT, "a pipelined frame's bounded wait for its partial pool gave up");
@@ -1403,6 +1412,13 @@ vr_status vr_render_frame(vr_ctx ctx, vr_volume vol, float *out_rgba, int out_on
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (ctx->mode == 1) return cycle_to(ctx, vol, out_rgba, out_on_device, s);
     return render_to(ctx, vol, out_rgba, out_on_device, s);
+}
+
+vr_status vr_debug_pipeline_gap(vr_ctx ctx)
+{
+    if (!ctx) return VR_ERR_ARG;
+    ctx->pool_frame += 2;
+    return VR_OK;
 }
 
 vr_status vr_set_frame_pipelining(vr_ctx ctx, int on)

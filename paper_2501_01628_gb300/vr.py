@@ -41,6 +41,7 @@ EXPORTS = (
     "vr_set_host_output_async", "vr_mesh_create", "vr_mesh_release", "vr_mesh_info",
     "vr_render_mesh_frame", "vr_debug_inject_fault", "vr_batch_debug_wait", "vr_set_march_staging",
     "vr_volume_create_share", "vr_composite_images", "vr_set_cell_layout", "vr_set_frame_pipelining",
+    "vr_debug_pipeline_gap",
 )
 
 
@@ -109,6 +110,7 @@ _SIG = {
     "vr_set_packet_width": (_I, [_P, _I]),
     "vr_set_march_staging": (_I, [_P, _I]),
     "vr_set_frame_pipelining": (_I, [_P, _I]),
+    "vr_debug_pipeline_gap": (_I, [_P]),
     "vr_set_cell_layout": (_I, [_P, _I]),
     "vr_set_host_output_async": (_I, [_P, _I]),
     "vr_render_backward": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -502,6 +504,11 @@ def vr_set_frame_pipelining(ctx, on: bool):
     """Consecutive vr_render_frame calls into device memory overlap (the next
     march starts in the previous frame's tail); same images. On by default."""
     _check(lib().vr_set_frame_pipelining(ctx, int(bool(on))), ctx, "vr_set_frame_pipelining")
+
+
+def vr_debug_pipeline_gap(ctx):
+    """Test hook: the next pipelined frame's bounded pool wait runs out."""
+    _check(lib().vr_debug_pipeline_gap(ctx), ctx, "vr_debug_pipeline_gap")
 
 
 def vr_set_cell_layout(ctx, layout: int):

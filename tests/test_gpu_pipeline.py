@@ -376,3 +376,37 @@ def test_pipelined_mesh_frames(vr):
                 vr.vr_volume_release(v)
             vr.vr_destroy(ctx)
     _assert_equal(res[False], res[True])
+
+
+def test_pipelined_pool_wait_runs_out_and_recovers(vr):
+    """The bounded pool wait of a pipelined march: a frame whose pool release
+    never comes (vr_debug_pipeline_gap) gives up within seconds, vr_sync returns
+    VR_ERR_TIMEOUT, and the frames after it equal the plain sequence's. Nothing
+    faults or hangs."""
+    import time
+    import torch
+    vol, tf, rng = _scene(n=32, seed=37)
+    part = dict(kind="grid", grid=(2, 2, 1))
+    cams = [synth.orbit_camera(48, 40, az) for az in (30.0, 150.0, 270.0)]
+    ctx, v = _ctx(vr, vol, part, tf, False, ert=0.99)
+    try:
+        want = _sequence(vr, ctx, v, cams)
+    finally:
+        _close(vr, ctx, v)
+    ctx, v = _ctx(vr, vol, part, tf, True, ert=0.99)
+    try:
+        first = _sequence(vr, ctx, v, cams)
+        _assert_equal(want, first)
+        vr.vr_debug_pipeline_gap(ctx)
+        vr.vr_set_camera(ctx, cams[0])
+        o = torch.empty((cams[0]["height"], cams[0]["width"], 4), device="cuda")
+        t0 = time.perf_counter()
+        vr.vr_render_frame(ctx, v, o)
+        with pytest.raises(vr.VrError) as e:
+            vr.vr_sync(ctx)
+        assert e.value.status == vr.VR_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 30.0
+        after = _sequence(vr, ctx, v, cams)
+        _assert_equal(want, after)
+    finally:
+        _close(vr, ctx, v)
